@@ -1,0 +1,865 @@
+/*
+ * fiber_oracle.c -- plain, slow FP64 reference of the ray / cubic-fiber
+ * intersection of Binder & Keller, "Fast, High Precision Ray/Fiber
+ * Intersection using Tight, Disjoint Bounding Volumes" (arXiv 1811.03374).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the CPU-baseline / reference leg of the benchmark may load this file.  It
+ * shares no code, header, table or helper with the CUDA library and includes
+ * nothing from it.
+ *
+ * Every function follows one passage of the paper, cited in its comment, and
+ * is written in the paper's notation: control points p0..p3 with the radius as
+ * fourth component (Sec. 3.3), the (p, d, t0, t1) representation and its
+ * subdivision rules (Sec. 3.1), the partitioned bounding cylinder (Sec. 3.2,
+ * Fig. 5), the unit-ray cylinder / plane tests (Sec. 3.3, App. A), the
+ * bit-string traversal (Sec. 3.3) and the curve constraints (Sec. 3.4,
+ * App. B.2).  Where the paper is silent or garbled the reading taken is named
+ * at the place it is used (readings R1..R19 in the design notes).
+ *
+ * Parity of each exported function is pinned by the oracle test suite
+ * (closed forms, brute force over leaves, golden values from the paper's
+ * figures, invariants).  Precision: double throughout; u intervals are exact
+ * dyadics start * 2^-23.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ROOT_SIZE (1u << 23) /* parametric domain [0,1] in units of 2^-23 */
+#define U_UNIT (1.0 / 8388608.0)
+
+typedef struct { double x, y, z, w; } v4;
+
+/* (p, d, t0, t1): p = p0, d = p3 - p0, t0 = p1 - p0, t1 = p3 - p2 (Sec. 3.1) */
+typedef struct { v4 p, d, t0, t1; } node_t;
+
+typedef struct {
+    double t, u;       /* distance along the unit ray, curve parameter */
+    int32_t hit;       /* 1 if a hit closer than the ray's t_max was found */
+    int32_t leaf;      /* start of the hit leaf in units of 2^-23 */
+    int32_t nodes;     /* node (pruning) tests performed */
+    int32_t descents;  /* partition + subdivide steps */
+    int32_t backtracks;/* jump_up + recompute steps */
+    int32_t pad;
+} orc_hit;
+
+/* ---------------------------------------------------------------- vectors */
+
+static v4 V(double x, double y, double z, double w) { v4 r = {x, y, z, w}; return r; }
+static v4 add4(v4 a, v4 b) { return V(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+static v4 sub4(v4 a, v4 b) { return V(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+static v4 mul4(double s, v4 a) { return V(s * a.x, s * a.y, s * a.z, s * a.w); }
+static double dot3(v4 a, v4 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+
+static v4 load_cp(const double *cp, int k) { return V(cp[4 * k], cp[4 * k + 1], cp[4 * k + 2], cp[4 * k + 3]); }
+
+/* ------------------------------------------------------- Bezier evaluation */
+
+/* Cubic Bezier point c(u) in Bernstein form (all four components). */
+static v4 bez_eval(const v4 P[4], double u)
+{
+    double v = 1.0 - u;
+    return add4(add4(mul4(v * v * v, P[0]), mul4(3.0 * u * v * v, P[1])),
+                add4(mul4(3.0 * u * u * v, P[2]), mul4(u * u * u, P[3])));
+}
+
+/* c'(u) / 3: the scaled derivative the paper evaluates (App. C). */
+static v4 bez_deriv3(const v4 P[4], double u)
+{
+    double v = 1.0 - u;
+    return add4(add4(mul4(v * v, sub4(P[1], P[0])), mul4(2.0 * u * v, sub4(P[2], P[1]))),
+                mul4(u * u, sub4(P[3], P[2])));
+}
+
+/* c''(u). */
+static v4 bez_deriv2(const v4 P[4], double u)
+{
+    v4 a = sub4(add4(P[2], P[0]), mul4(2.0, P[1]));
+    v4 b = sub4(add4(P[3], P[1]), mul4(2.0, P[2]));
+    return mul4(6.0, add4(mul4(1.0 - u, a), mul4(u, b)));
+}
+
+/* ------------------------------------------------------------ ray frame */
+
+/*
+ * Orthonormal frame (e1, e2, w) around the unit direction w.  Sec. 3.3 uses
+ * Duff et al.'s construction; any orthonormal completion gives the same
+ * result, because every quantity the method uses (a_x p_y - a_y p_x,
+ * a_x^2 + a_y^2, dot products, z components) is invariant under rotation
+ * about the ray.  This one is Gram-Schmidt against the least aligned axis.
+ */
+static void ray_frame(const double w[3], double e1[3], double e2[3])
+{
+    double a[3] = {0.0, 0.0, 0.0};
+    double ax = fabs(w[0]), ay = fabs(w[1]), az = fabs(w[2]);
+    if (ax <= ay && ax <= az) a[0] = 1.0;
+    else if (ay <= az) a[1] = 1.0;
+    else a[2] = 1.0;
+    double k = a[0] * w[0] + a[1] * w[1] + a[2] * w[2];
+    double q[3] = {a[0] - k * w[0], a[1] - k * w[1], a[2] - k * w[2]};
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    for (int i = 0; i < 3; ++i) e1[i] = q[i] / n;
+    e2[0] = w[1] * e1[2] - w[2] * e1[1];
+    e2[1] = w[2] * e1[0] - w[0] * e1[2];
+    e2[2] = w[0] * e1[1] - w[1] * e1[0];
+}
+
+typedef struct { double o[3], w[3], e1[3], e2[3], tmax; } ray_t;
+
+/* Ray from 8 floats {o, t_max, w, 0}; the direction is normalised (unit ray, Sec. 3.3). */
+static ray_t make_ray_f(const float *r8)
+{
+    ray_t r;
+    double n = sqrt((double)r8[4] * r8[4] + (double)r8[5] * r8[5] + (double)r8[6] * r8[6]);
+    for (int i = 0; i < 3; ++i) { r.o[i] = r8[i]; r.w[i] = r8[4 + i] / n; }
+    r.tmax = r8[3];
+    ray_frame(r.w, r.e1, r.e2);
+    return r;
+}
+
+static ray_t make_ray_d(const double *r7)
+{
+    ray_t r;
+    double n = sqrt(r7[3] * r7[3] + r7[4] * r7[4] + r7[5] * r7[5]);
+    for (int i = 0; i < 3; ++i) { r.o[i] = r7[i]; r.w[i] = r7[3 + i] / n; }
+    r.tmax = r7[6];
+    ray_frame(r.w, r.e1, r.e2);
+    return r;
+}
+
+/* Control points in the ray-centric frame: the ray starts at the origin and
+ * runs along +z; the radius is carried unchanged (Sec. 3.3, reading R8). */
+static void to_ray_frame(const ray_t *r, const double *cp, v4 Q[4])
+{
+    for (int k = 0; k < 4; ++k) {
+        double q[3] = {cp[4 * k] - r->o[0], cp[4 * k + 1] - r->o[1], cp[4 * k + 2] - r->o[2]};
+        Q[k].x = q[0] * r->e1[0] + q[1] * r->e1[1] + q[2] * r->e1[2];
+        Q[k].y = q[0] * r->e2[0] + q[1] * r->e2[1] + q[2] * r->e2[2];
+        Q[k].z = q[0] * r->w[0] + q[1] * r->w[1] + q[2] * r->w[2];
+        Q[k].w = cp[4 * k + 3];
+    }
+}
+
+/* ---------------------------------------------------------- primitives */
+
+/* Unit ray against the plane through p with normal n: t = <n, p> / n_z
+ * (Sec. 3.3).  Returns 0 when n_z == 0 (plane parallel to the ray). */
+static int plane_t(v4 p, v4 n, double *t)
+{
+    if (n.z == 0.0) return 0;
+    *t = dot3(n, p) / n.z;
+    return 1;
+}
+
+/*
+ * Unit ray against the infinite cylinder of radius r through p along a
+ * (App. A): g = a_x^2 + a_y^2, squared distance (a_x p_y - a_y p_x)^2 / g,
+ * t_cpa = p_z - a_z (a_x p_x + a_y p_y) / g, s = sqrt((r^2 - d^2)(a_z^2 + g) / g),
+ * hits at t_cpa -+ s.  Axis parallel to the ray (g == 0): inside gives
+ * (-inf, +inf), outside is a miss (reading R3).  Returns 0 on a miss.
+ */
+static int cylinder(v4 p, v4 a, double r, double *c0, double *c1)
+{
+    double g = a.x * a.x + a.y * a.y;
+    if (g == 0.0) {
+        if (p.x * p.x + p.y * p.y < r * r) { *c0 = -INFINITY; *c1 = INFINITY; return 1; }
+        return 0;
+    }
+    double cr = a.x * p.y - a.y * p.x;
+    double e = r * r - cr * cr / g;
+    if (e < 0.0) return 0;
+    double tcpa = p.z - a.z * (a.x * p.x + a.y * p.y) / g;
+    double s = sqrt(e * (a.z * a.z + g) / g);
+    *c0 = tcpa - s;
+    *c1 = tcpa + s;
+    return 1;
+}
+
+/*
+ * Conservative radius of the bounding cylinder along (p, p + d): the larger
+ * distance of the two inner control points from the axis plus the largest
+ * control radius (Sec. 3.3, convex hull property).  Inner points relative to p
+ * are t0 and d - t1, whose distances from the axis equal those of t0 and t1.
+ * Zero-length axis: distance from p (reading).
+ */
+static double cons_radius(const node_t *c)
+{
+    double dd = dot3(c->d, c->d), m;
+    if (dd > 0.0) {
+        double b0 = dot3(c->t0, c->d) / dd, b1 = dot3(c->t1, c->d) / dd;
+        v4 q0 = sub4(c->t0, mul4(b0, c->d)), q1 = sub4(c->t1, mul4(b1, c->d));
+        m = dmax(dot3(q0, q0), dot3(q1, q1));
+    } else {
+        m = dmax(dot3(c->t0, c->t0), dot3(c->t1, c->t1));
+    }
+    /* radii of the control points: r0 = p.w, r1 = p.w + t0.w, r3 = p.w + d.w,
+       r2 = r3 - t1.w */
+    double rmax = c->p.w + dmax(dmax(0.0, c->t0.w), dmax(c->d.w, c->d.w - c->t1.w));
+    return sqrt(m) + rmax;
+}
+
+/*
+ * t-interval of the region between the cropping planes: the start plane
+ * through p with normal t0 (kept side <x - p, t0> >= 0) and the end plane
+ * through p + d with normal t1 (kept side <x - p - d, t1> <= 0), clipped to
+ * [0, ray_tmax] (Sec. 3.3).  A plane parallel to the ray either leaves the
+ * interval alone or, if the ray lies on its excluded side, empties it
+ * (reading R4).  Returns 0 for an empty interval.
+ */
+static int slab(const node_t *c, double ray_tmax, double *tmin, double *tmax)
+{
+    double lo = 0.0, hi = ray_tmax, t;
+    if (plane_t(c->p, c->t0, &t)) {
+        if (c->t0.z > 0.0) lo = dmax(lo, t);
+        else hi = dmin(hi, t);
+    } else if (-dot3(c->p, c->t0) < 0.0) {
+        lo = INFINITY;
+    }
+    v4 q = add4(c->p, c->d);
+    if (plane_t(q, c->t1, &t)) {
+        if (c->t1.z < 0.0) lo = dmax(lo, t);
+        else hi = dmin(hi, t);
+    } else if (-dot3(q, c->t1) > 0.0) {
+        lo = INFINITY;
+    }
+    *tmin = lo;
+    *tmax = hi;
+    return lo <= hi;
+}
+
+/* Subdivision of (p, d, t0, t1) at the domain centre (Sec. 3.1):
+ * dp = 3/8 t0 + 1/2 d - 3/8 t1, tc = -1/8 t0 + 1/4 d - 1/8 t1;
+ * left = (p, dp, t0/2, tc), right = (p + dp, d - dp, tc, t1/2). */
+static void split_terms(const node_t *c, v4 *dp, v4 *tc)
+{
+    *dp = add4(add4(mul4(0.375, c->t0), mul4(0.5, c->d)), mul4(-0.375, c->t1));
+    *tc = add4(add4(mul4(-0.125, c->t0), mul4(0.25, c->d)), mul4(-0.125, c->t1));
+}
+
+static void subdivide(node_t *c, int go_right, v4 dp, v4 tc)
+{
+    if (go_right) {
+        c->p = add4(c->p, dp);
+        c->d = sub4(c->d, dp);
+        c->t0 = tc;
+        c->t1 = mul4(0.5, c->t1);
+    } else {
+        c->d = dp;
+        c->t0 = mul4(0.5, c->t0);
+        c->t1 = tc;
+    }
+}
+
+/* Node of the sub-interval [u0, u1] (start, size in units of 2^-23),
+ * recomputed from the curve after backtracking (Sec. 3.3):
+ * p = c(u0), d = c(u1) - c(u0), t0,1 = (u1 - u0) c'(u0,1) / 3. */
+static void node_at(const v4 Q[4], uint32_t start, uint32_t size, node_t *c)
+{
+    double u0 = start * U_UNIT, u1 = (double)(start + size) * U_UNIT;
+    v4 a = bez_eval(Q, u0), b = bez_eval(Q, u1);
+    c->p = a;
+    c->d = sub4(b, a);
+    c->t0 = mul4(u1 - u0, bez_deriv3(Q, u0));
+    c->t1 = mul4(u1 - u0, bez_deriv3(Q, u1));
+}
+
+/* Conversion {p0, p1, p2, p3} -> {p, d, t0, t1} (Sec. 3.1). */
+static void node_of_points(const v4 Q[4], node_t *c)
+{
+    c->p = Q[0];
+    c->d = sub4(Q[3], Q[0]);
+    c->t0 = sub4(Q[1], Q[0]);
+    c->t1 = sub4(Q[3], Q[2]);
+}
+
+/* ----------------------------------------------------------- traversal */
+
+/*
+ * Closest hit of a unit ray with one curve (Sec. 3, Sec. 3.2-3.3, the
+ * iterative routine of App. C), curve already in the ray frame.
+ *
+ * State: the current node, its t-interval [tmin, tmax], the bit string (one
+ * bit per level, set iff both children must be visited), and the integer
+ * interval (start, size).  Each step tests the node's bounding cylinder
+ * against the interval:
+ *   - overlap and size <= min_size: leaf; the hit is the entry into the
+ *     capped leaf cylinder, max(c0, tmin) (reading R1); stop (immediate
+ *     termination, Sec. 3.2);
+ *   - overlap otherwise: partition by the plane through the split point with
+ *     normal tc, continue with the child the ray reaches first, tighten one
+ *     bound of the interval, set the bit if the ray crosses the plane inside
+ *     the cylinder (Sec. 3.2, Fig. 5);
+ *   - no overlap: if no bit is set, stop; otherwise jump to the sibling at the
+ *     deepest set bit and recompute its node and interval.
+ * Overlap means the cylinder is hit and max(c0, tmin) <= min(c1, tmax): the
+ * listing's comparisons plus non-emptiness of both intervals (reading R5).
+ */
+static void traverse(const v4 Q[4], int depth, double ray_tmax, orc_hit *h)
+{
+    node_t c;
+    node_of_points(Q, &c);
+    uint32_t bits = 0, size = ROOT_SIZE, start = 0;
+    uint32_t min_size = ROOT_SIZE >> depth;
+    double tmin, tmax, t = INFINITY;
+    int hit = 0;
+    slab(&c, ray_tmax, &tmin, &tmax);
+    h->nodes = h->descents = h->backtracks = 0;
+    for (;;) {
+        double r = cons_radius(&c), c0 = 0.0, c1 = 0.0;
+        h->nodes++;
+        int over = cylinder(c.p, c.d, r, &c0, &c1) && dmax(c0, tmin) <= dmin(c1, tmax);
+        if (over) {
+            if (size <= min_size) {
+                t = dmax(c0, tmin);
+                hit = 1;
+                break;
+            }
+            v4 dp, tc;
+            split_terms(&c, &dp, &tc);
+            v4 s = add4(c.p, dp);
+            double tp;
+            int go_right, both;
+            if (plane_t(s, tc, &tp)) {
+                go_right = (tp > c0) != (tc.z > 0.0);
+                both = (c0 < tp) && (c1 > tp);
+                if (tp > c0) tmax = dmin(tmax, tp);
+                else tmin = dmax(tmin, tp);
+            } else {
+                /* plane parallel to the ray: the ray stays on the origin's side (R4) */
+                go_right = -dot3(s, tc) >= 0.0;
+                both = 0;
+            }
+            subdivide(&c, go_right, dp, tc);
+            size >>= 1;
+            if (both) bits ^= size;
+            if (go_right) start ^= size;
+            h->descents++;
+        } else {
+            if (!bits) break;
+            size = bits & (~bits + 1u); /* lowest set bit: deepest pending level */
+            start ^= size;
+            bits ^= size;
+            start &= ~(size - 1u);
+            node_at(Q, start, size, &c);
+            slab(&c, ray_tmax, &tmin, &tmax);
+            h->backtracks++;
+        }
+    }
+    h->hit = 0;
+    h->t = INFINITY;
+    h->u = -1.0;
+    h->leaf = -1;
+    if (hit && t < ray_tmax) {
+        /* u: projection of the hit point onto the leaf axis (App. C) */
+        double dd = dot3(c.d, c.d);
+        double ul = 0.0;
+        if (dd > 0.0) {
+            v4 hb = V(-c.p.x, -c.p.y, t - c.p.z, 0.0);
+            ul = dot3(hb, c.d) / dd;
+            ul = dmax(0.0, dmin(1.0, ul));
+        }
+        double u0 = start * U_UNIT, u1 = (double)(start + size) * U_UNIT;
+        h->hit = 1;
+        h->t = t;
+        h->u = u0 + ul * (u1 - u0);
+        h->leaf = (int32_t)start;
+    }
+}
+
+/* ------------------------------------------------- curve constraints */
+
+/* The five inequalities of Sec. 3.4 / App. B.2 on the positions. */
+int orc_valid_cubic(const double *cp)
+{
+    v4 P[4];
+    for (int k = 0; k < 4; ++k) P[k] = load_cp(cp, k);
+    v4 p20 = sub4(P[2], P[0]), p10 = sub4(P[1], P[0]), p31 = sub4(P[3], P[1]), p32 = sub4(P[3], P[2]);
+    return dot3(p20, p10) >= 0.0 && dot3(p31, p10) >= 0.0 && dot3(p31, p32) >= 0.0 &&
+           dot3(p20, p32) >= 0.0 && dot3(p20, p31) >= 0.0;
+}
+
+static double norm3(v4 a) { return sqrt(dot3(a, a)); }
+
+/*
+ * Sampled end-plane check for thick fibers (Sec. 3.4, Fig. 7; reading R13).
+ * The fiber surface point at parameter u nearest the end plane lies in the
+ * normal plane at u, displaced by the largest radius rbar along the
+ * Gram-Schmidt projection n_u of the plane normal.  The end plane through p3
+ * (normal c'(1)) crops the surface if <p3 - c(u), t1^> < rbar |t1^ - <t1^, tu^> tu^|
+ * for some u; likewise for the start plane through p0.  Checked at u = i/32
+ * and, at the end points themselves, as rbar * curvature < 1.  A zero end
+ * tangent fails.
+ */
+#define THICK_SAMPLES 32
+int orc_thick_ok(const double *cp)
+{
+    v4 P[4];
+    double rbar = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        P[k] = load_cp(cp, k);
+        rbar = dmax(rbar, P[k].w);
+    }
+    v4 ta = bez_deriv3(P, 0.0), tb = bez_deriv3(P, 1.0);
+    double la = norm3(ta), lb = norm3(tb);
+    if (!(la > 0.0) || !(lb > 0.0)) return 0;
+    v4 na = mul4(1.0 / la, ta), nb = mul4(1.0 / lb, tb);
+    for (int i = 0; i <= THICK_SAMPLES; ++i) {
+        double u = (double)i / THICK_SAMPLES;
+        v4 tu = bez_deriv3(P, u);
+        double lu = norm3(tu);
+        if (!(lu > 0.0)) return 0;
+        v4 nu = mul4(1.0 / lu, tu);
+        v4 cu = bez_eval(P, u);
+        if (i < THICK_SAMPLES) { /* end plane */
+            v4 g = sub4(nb, mul4(dot3(nb, nu), nu));
+            if (dot3(sub4(P[3], cu), nb) < rbar * norm3(g)) return 0;
+        }
+        if (i > 0) { /* start plane */
+            v4 g = sub4(na, mul4(dot3(na, nu), nu));
+            if (dot3(sub4(cu, P[0]), na) < rbar * norm3(g)) return 0;
+        }
+    }
+    for (int e = 0; e < 2; ++e) {
+        double u = (double)e;
+        v4 d1 = mul4(3.0, bez_deriv3(P, u)), d2 = bez_deriv2(P, u);
+        v4 cr = V(d1.y * d2.z - d1.z * d2.y, d1.z * d2.x - d1.x * d2.z, d1.x * d2.y - d1.y * d2.x, 0.0);
+        double l1 = norm3(d1);
+        double kappa = norm3(cr) / (l1 * l1 * l1);
+        if (rbar * kappa >= 1.0) return 0;
+    }
+    return 1;
+}
+
+/* De Casteljau halving at u = 1/2, all four components (App. B.2). */
+void orc_split_half(const double *cp, double *L, double *R)
+{
+    for (int a = 0; a < 4; ++a) {
+        double p0 = cp[a], p1 = cp[4 + a], p2 = cp[8 + a], p3 = cp[12 + a];
+        double p01 = 0.5 * (p0 + p1), p12 = 0.5 * (p1 + p2), p23 = 0.5 * (p2 + p3);
+        double p012 = 0.5 * (p01 + p12), p123 = 0.5 * (p12 + p23);
+        double s = 0.5 * (p012 + p123);
+        L[a] = p0; L[4 + a] = p01; L[8 + a] = p012; L[12 + a] = s;
+        R[a] = s; R[4 + a] = p123; R[8 + a] = p23; R[12 + a] = p3;
+    }
+}
+
+/*
+ * Pre-split (Sec. 3.4: curves violating the constraints "must be subdivided
+ * beforehand"; reading R15): a curve failing the constraints or the sampled
+ * thick-fiber check is halved at u = 1/2, recursively, left before right, up
+ * to max_level levels.  A piece still failing at max_level is kept and
+ * flagged unsupported (flag bit 0).
+ */
+typedef struct {
+    double *cp;
+    int32_t *seg, *level, *off, *flags;
+    int64_t n, cap;
+} piece_out;
+
+static void presplit_rec(const double *cp, int32_t seg, int level, int32_t off, int max_level,
+                         int thick, piece_out *o)
+{
+    int ok = orc_valid_cubic(cp) && (!thick || orc_thick_ok(cp));
+    if (ok || level >= max_level) {
+        if (o->n < o->cap) {
+            memcpy(o->cp + 16 * o->n, cp, 16 * sizeof(double));
+            o->seg[o->n] = seg;
+            o->level[o->n] = level;
+            o->off[o->n] = off;
+            o->flags[o->n] = ok ? 0 : 1;
+        }
+        o->n++;
+        return;
+    }
+    double L[16], R[16];
+    orc_split_half(cp, L, R);
+    presplit_rec(L, seg, level + 1, 2 * off, max_level, thick, o);
+    presplit_rec(R, seg, level + 1, 2 * off + 1, max_level, thick, o);
+}
+
+/* cps: n_seg x 16 floats.  Returns the number of pieces (written if <= cap). */
+int64_t orc_presplit(const float *cps, int64_t n_seg, int max_level, int thick, double *piece_cp,
+                     int32_t *piece_seg, int32_t *piece_level, int32_t *piece_off,
+                     int32_t *piece_flags, int64_t cap)
+{
+    piece_out o = {piece_cp, piece_seg, piece_level, piece_off, piece_flags, 0, cap};
+    for (int64_t s = 0; s < n_seg; ++s) {
+        double cp[16];
+        for (int i = 0; i < 16; ++i) cp[i] = cps[16 * s + i];
+        presplit_rec(cp, (int32_t)s, 0, 0, max_level, thick, &o);
+    }
+    return o.n;
+}
+
+/* ------------------------------------------------------ exported entries */
+
+/* One ray (7 doubles: o, w, t_max) against one curve at the given depth. */
+void orc_intersect(const double *ray7, const double *cp, int depth, orc_hit *h)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 Q[4];
+    to_ray_frame(&r, cp, Q);
+    traverse(Q, depth, r.tmax, h);
+}
+
+static int piece_depth(int depth, int level) { return depth > level ? depth - level : 0; }
+
+/*
+ * Closest hit per ray over its CSR candidates (Sec. 3.2, immediate
+ * termination; Sec. 4 "closer segments are always intersected first" applied
+ * across candidates): candidates in row order, pieces of a segment in order;
+ * the best t so far is the t_max of the next test (reading R7) and only a
+ * strictly closer hit replaces it, so ties keep the earlier candidate.
+ * Outputs t (inf on miss), u in the segment's parameter (-1), segment (-1),
+ * leaf start in units of 2^-23 of the segment (-1).  counters (nullable):
+ * [nodes, descents, backtracks, hits, tests].
+ */
+void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+                 const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+                 const int32_t *piece_off, int depth, int nthreads, double *t_out, double *u_out,
+                 int32_t *seg_out, int32_t *leaf_out, int64_t *counters)
+{
+    int64_t cn = 0, cd = 0, cb = 0, ch = 0, ct = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : cn, cd, cb, ch, ct)
+    for (int64_t i = 0; i < n_ray; ++i) {
+        ray_t r = make_ray_f(rays + 8 * i);
+        double best = r.tmax, bu = -1.0;
+        int32_t bs = -1, bl = -1;
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+            int32_t s = seg_idx[j];
+            for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
+                v4 Q[4];
+                orc_hit h;
+                to_ray_frame(&r, piece_cp + 16 * k, Q);
+                int lv = piece_level[k];
+                traverse(Q, piece_depth(depth, lv), best, &h);
+                cn += h.nodes; cd += h.descents; cb += h.backtracks; ct += 1;
+                if (h.hit && h.t < best) {
+                    double scale = ldexp(1.0, -lv);
+                    best = h.t;
+                    bu = (piece_off[k] + h.u) * scale;
+                    bs = s;
+                    bl = (int32_t)(((int64_t)piece_off[k] << (23 - lv)) + (h.leaf >> lv));
+                }
+            }
+        }
+        if (bs >= 0) ch += 1;
+        t_out[i] = bs >= 0 ? best : INFINITY;
+        u_out[i] = bu;
+        seg_out[i] = bs;
+        if (leaf_out) leaf_out[i] = bl;
+    }
+    if (counters) {
+        counters[0] = cn; counters[1] = cd; counters[2] = cb; counters[3] = ch; counters[4] = ct;
+    }
+}
+
+/* Per-pair hits: each candidate tested with the ray's own t_max; pieces of a
+ * segment combined by the closest rule above.  Outputs indexed by pair. */
+void orc_pairs(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+               const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+               const int32_t *piece_off, int depth, int nthreads, double *t_out, double *u_out,
+               int32_t *leaf_out, int64_t *counters)
+{
+    int64_t cn = 0, cd = 0, cb = 0, ch = 0, ct = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : cn, cd, cb, ch, ct)
+    for (int64_t i = 0; i < n_ray; ++i) {
+        ray_t r = make_ray_f(rays + 8 * i);
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+            int32_t s = seg_idx[j];
+            double best = r.tmax, bu = -1.0;
+            int32_t bl = -1, got = 0;
+            for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
+                v4 Q[4];
+                orc_hit h;
+                to_ray_frame(&r, piece_cp + 16 * k, Q);
+                int lv = piece_level[k];
+                traverse(Q, piece_depth(depth, lv), best, &h);
+                cn += h.nodes; cd += h.descents; cb += h.backtracks; ct += 1;
+                if (h.hit && h.t < best) {
+                    best = h.t;
+                    bu = (piece_off[k] + h.u) * ldexp(1.0, -lv);
+                    bl = (int32_t)(((int64_t)piece_off[k] << (23 - lv)) + (h.leaf >> lv));
+                    got = 1;
+                }
+            }
+            ch += got;
+            t_out[j] = got ? best : INFINITY;
+            u_out[j] = bu;
+            if (leaf_out) leaf_out[j] = bl;
+        }
+    }
+    if (counters) {
+        counters[0] = cn; counters[1] = cd; counters[2] = cb; counters[3] = ch; counters[4] = ct;
+    }
+}
+
+/* ---------------------------------------------------- internals for pins */
+
+void orc_to_ray_frame(const double *ray7, const double *cp, double *out16)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 Q[4];
+    to_ray_frame(&r, cp, Q);
+    for (int k = 0; k < 4; ++k) {
+        out16[4 * k] = Q[k].x; out16[4 * k + 1] = Q[k].y; out16[4 * k + 2] = Q[k].z; out16[4 * k + 3] = Q[k].w;
+    }
+}
+
+static void node_store(const node_t *c, double *o)
+{
+    const v4 *v[4] = {&c->p, &c->d, &c->t0, &c->t1};
+    for (int k = 0; k < 4; ++k) { o[4 * k] = v[k]->x; o[4 * k + 1] = v[k]->y; o[4 * k + 2] = v[k]->z; o[4 * k + 3] = v[k]->w; }
+}
+
+static void node_load(const double *o, node_t *c)
+{
+    v4 *v[4] = {&c->p, &c->d, &c->t0, &c->t1};
+    for (int k = 0; k < 4; ++k) *v[k] = V(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+}
+
+/* Node (p, d, t0, t1) of the sub-interval (start, size) of the curve cp. */
+void orc_node_at(const double *cp, uint32_t start, uint32_t size, double *out16)
+{
+    v4 P[4];
+    node_t c;
+    for (int k = 0; k < 4; ++k) P[k] = load_cp(cp, k);
+    if (start == 0 && size == ROOT_SIZE) node_of_points(P, &c);
+    else node_at(P, start, size, &c);
+    node_store(&c, out16);
+}
+
+/* One subdivision step applied to a node (left or right child). */
+void orc_subdivide(const double *node16, int go_right, double *out16)
+{
+    node_t c;
+    v4 dp, tc;
+    node_load(node16, &c);
+    split_terms(&c, &dp, &tc);
+    subdivide(&c, go_right, dp, tc);
+    node_store(&c, out16);
+}
+
+double orc_cons_radius(const double *node16)
+{
+    node_t c;
+    node_load(node16, &c);
+    return cons_radius(&c);
+}
+
+int orc_cylinder(const double *p3, const double *a3, double r, double *out2)
+{
+    return cylinder(V(p3[0], p3[1], p3[2], 0.0), V(a3[0], a3[1], a3[2], 0.0), r, &out2[0], &out2[1]);
+}
+
+int orc_slab(const double *node16, double ray_tmax, double *out2)
+{
+    node_t c;
+    node_load(node16, &c);
+    return slab(&c, ray_tmax, &out2[0], &out2[1]);
+}
+
+/*
+ * The capped cylinder of one leaf, tested on its own: the leaf's node from
+ * node_at, its conservative radius and its own end-plane interval.  This is
+ * the plain definition of a leaf bounding volume (Sec. 3.3); the brute-force
+ * pin enumerates it over all 2^depth leaves.  Returns 1 and the entry t and u
+ * (projection onto the leaf axis) if the ray meets it.
+ */
+int orc_leaf_hit(const double *ray7, const double *cp, int depth, uint32_t leaf, double *t_out,
+                 double *u_out)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 Q[4];
+    node_t c;
+    to_ray_frame(&r, cp, Q);
+    uint32_t size = ROOT_SIZE >> depth, start = leaf * size;
+    if (start == 0 && size == ROOT_SIZE) node_of_points(Q, &c);
+    else node_at(Q, start, size, &c);
+    double tmin, tmax, c0, c1;
+    slab(&c, r.tmax, &tmin, &tmax);
+    double rad = cons_radius(&c);
+    if (!(cylinder(c.p, c.d, rad, &c0, &c1) && dmax(c0, tmin) <= dmin(c1, tmax))) return 0;
+    double t = dmax(c0, tmin);
+    double dd = dot3(c.d, c.d), ul = 0.0;
+    if (dd > 0.0) ul = dmax(0.0, dmin(1.0, (-c.p.x * c.d.x - c.p.y * c.d.y + (t - c.p.z) * c.d.z) / dd));
+    *t_out = t;
+    *u_out = (start + ul * size) * U_UNIT;
+    return 1;
+}
+
+/* ---------------------------------------------------------- limit surface */
+
+/*
+ * The surface the leaf cylinders converge to as the depth grows (Sec. 3.2:
+ * the cylinders' limit surface; reading R19): circles of radius r(u) in the
+ * plane through c(u) normal to c'(u), closed by the flat end disks at u = 0
+ * and u = 1.  With x = o + t w:
+ *   G1(t, u) = <x - c(u), c'(u)> = 0,   G2(t, u) = |x - c(u)|^2 - r(u)^2 = 0.
+ * G1 is linear in t; h(u) = G2(t(u), u) is sampled on n_grid + 1 points, every
+ * sign change is bisected to 1e-15 in u and polished by two-dimensional
+ * Newton steps.  Returns 1 (lateral), 2 (end disk at u = 0), 3 (u = 1) or 0.
+ */
+static void cps_world(const double *cp, v4 P[4])
+{
+    for (int k = 0; k < 4; ++k) P[k] = load_cp(cp, k);
+}
+
+static int t_of_u(const ray_t *r, const v4 P[4], double u, double *t, double *h)
+{
+    v4 c = bez_eval(P, u), d1 = mul4(3.0, bez_deriv3(P, u));
+    v4 o = V(r->o[0], r->o[1], r->o[2], 0.0), w = V(r->w[0], r->w[1], r->w[2], 0.0);
+    double den = dot3(w, d1);
+    if (den == 0.0) return 0;
+    *t = dot3(sub4(c, o), d1) / den;
+    v4 x = add4(o, mul4(*t, w));
+    v4 e = sub4(x, c);
+    *h = dot3(e, e) - c.w * c.w;
+    return 1;
+}
+
+static void newton_tu(const ray_t *r, const v4 P[4], double *t, double *u, int iters)
+{
+    v4 o = V(r->o[0], r->o[1], r->o[2], 0.0), w = V(r->w[0], r->w[1], r->w[2], 0.0);
+    for (int it = 0; it < iters; ++it) {
+        v4 c = bez_eval(P, *u), d1 = mul4(3.0, bez_deriv3(P, *u)), d2 = bez_deriv2(P, *u);
+        v4 e = sub4(add4(o, mul4(*t, w)), c);
+        double G1 = dot3(e, d1), G2 = dot3(e, e) - c.w * c.w;
+        double J00 = dot3(w, d1), J01 = dot3(e, d2) - dot3(d1, d1);
+        double J10 = 2.0 * dot3(e, w), J11 = -2.0 * dot3(e, d1) - 2.0 * c.w * d1.w;
+        double det = J00 * J11 - J01 * J10;
+        if (det == 0.0 || !isfinite(det)) return;
+        double dt = (J11 * G1 - J01 * G2) / det, du = (-J10 * G1 + J00 * G2) / det;
+        *t -= dt;
+        *u -= du;
+    }
+}
+
+int orc_limit_hit(const double *ray7, const double *cp, int n_grid, double *t_out, double *u_out)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 P[4];
+    cps_world(cp, P);
+    double best = INFINITY, bu = -1.0;
+    int kind = 0;
+    double tp = 0.0, hp = 0.0;
+    int okp = t_of_u(&r, P, 0.0, &tp, &hp);
+    for (int i = 1; i <= n_grid; ++i) {
+        double u = (double)i / n_grid, t = 0.0, h = 0.0;
+        int ok = t_of_u(&r, P, u, &t, &h);
+        if (ok && okp && ((hp <= 0.0) != (h <= 0.0))) {
+            double a = (double)(i - 1) / n_grid, b = u, ha = hp;
+            /* no pole of t(u) inside: the denominators keep their sign */
+            v4 wv = V(r.w[0], r.w[1], r.w[2], 0.0);
+            double da = dot3(wv, bez_deriv3(P, a)), db = dot3(wv, bez_deriv3(P, b));
+            if ((da > 0.0) == (db > 0.0)) {
+                for (int it = 0; it < 200 && b - a > 1e-15; ++it) {
+                    double m = 0.5 * (a + b), tm, hm;
+                    if (!t_of_u(&r, P, m, &tm, &hm)) break;
+                    if ((hm <= 0.0) == (ha <= 0.0)) { a = m; ha = hm; }
+                    else b = m;
+                }
+                double uu = 0.5 * (a + b), tt, hh;
+                if (t_of_u(&r, P, uu, &tt, &hh)) {
+                    newton_tu(&r, P, &tt, &uu, 3);
+                    if (tt >= 0.0 && tt < r.tmax && tt < best && uu >= 0.0 && uu <= 1.0) {
+                        best = tt; bu = uu; kind = 1;
+                    }
+                }
+            }
+        }
+        okp = ok; tp = t; hp = h;
+    }
+    for (int e = 0; e < 2; ++e) {
+        double u = (double)e, t, h;
+        if (t_of_u(&r, P, u, &t, &h) && h <= 0.0 && t >= 0.0 && t < r.tmax && t < best) {
+            best = t; bu = u; kind = 2 + e;
+        }
+    }
+    *t_out = best;
+    *u_out = bu;
+    return kind;
+}
+
+/*
+ * dt / d(p_k, r_k) at a hit of the limit surface (reading R19), by the
+ * implicit function theorem on G(t, u; theta) = 0:
+ *   [dt, du]^T = -J^{-1} dG/dtheta,  J = dG/d(t, u),
+ *   dG1/dp_k = -B_k c' + B_k' (x - c),  dG2/dp_k = -2 B_k (x - c),
+ *   dG2/dr_k = -2 r B_k,  dG1/dr_k = 0.
+ * End-disk hits (u exactly 0 or 1) use G1 alone with u fixed.  (t, u) are
+ * first refined by Newton steps.  grad: 16 doubles (p_k.xyz, r_k per k).
+ * Returns 1 on success, 0 for a singular system.
+ */
+int orc_grad_t(const double *ray7, const double *cp, double t, double u, double *grad)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 P[4];
+    cps_world(cp, P);
+    v4 o = V(r.o[0], r.o[1], r.o[2], 0.0), w = V(r.w[0], r.w[1], r.w[2], 0.0);
+    int cap = (u == 0.0 || u == 1.0);
+    if (!cap) newton_tu(&r, P, &t, &u, 4);
+    v4 c = bez_eval(P, u), d1 = mul4(3.0, bez_deriv3(P, u)), d2 = bez_deriv2(P, u);
+    v4 e = sub4(add4(o, mul4(t, w)), c);
+    double v = 1.0 - u;
+    double B[4] = {v * v * v, 3.0 * u * v * v, 3.0 * u * u * v, u * u * u};
+    double dB[4] = {-3.0 * v * v, 3.0 * v * v - 6.0 * u * v, 6.0 * u * v - 3.0 * u * u, 3.0 * u * u};
+    double a1, a2; /* dt/dtheta = -(a1 dG1/dtheta + a2 dG2/dtheta) */
+    if (cap) {
+        double J00 = dot3(w, d1);
+        if (J00 == 0.0) return 0;
+        a1 = 1.0 / J00;
+        a2 = 0.0;
+    } else {
+        double J00 = dot3(w, d1), J01 = dot3(e, d2) - dot3(d1, d1);
+        double J10 = 2.0 * dot3(e, w), J11 = -2.0 * dot3(e, d1) - 2.0 * c.w * d1.w;
+        double det = J00 * J11 - J01 * J10;
+        if (det == 0.0 || !isfinite(det)) return 0;
+        a1 = J11 / det;
+        a2 = -J01 / det;
+    }
+    for (int k = 0; k < 4; ++k) {
+        v4 g1 = sub4(mul4(dB[k], e), mul4(B[k], d1));
+        v4 g2 = mul4(-2.0 * B[k], e);
+        grad[4 * k + 0] = -(a1 * g1.x + a2 * g2.x);
+        grad[4 * k + 1] = -(a1 * g1.y + a2 * g2.y);
+        grad[4 * k + 2] = -(a1 * g1.z + a2 * g2.z);
+        grad[4 * k + 3] = -(a2 * (-2.0 * c.w * B[k]));
+    }
+    return 1;
+}
+
+/* Refined (t, u) of a lateral limit-surface hit near the given estimate. */
+void orc_refine_hit(const double *ray7, const double *cp, double *t, double *u)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 P[4];
+    cps_world(cp, P);
+    newton_tu(&r, P, t, u, 6);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
