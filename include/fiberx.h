@@ -1,0 +1,216 @@
+/*
+ * fiberx.h -- C ABI of the GB300 (sm_103a) ray / cubic-fiber intersector.
+ *
+ * Method: Binder & Keller, "Fast, High Precision Ray/Fiber Intersection using
+ * Tight, Disjoint Bounding Volumes" (arXiv 1811.03374).  A fiber segment is a
+ * cubic Bezier curve with a radius per control point (Sec. 3.3).  A ray is
+ * intersected with a segment by stackless recursive subdivision (Sec. 3, the
+ * iterative routine of App. C): each region is bounded by a cylinder along its
+ * chord with a conservative radius (Sec. 3.3), partitioned by the plane through
+ * the split point orthogonal to the split tangent (Sec. 3.2, Fig. 5); the child
+ * the ray reaches first is visited first, one bit per level records whether
+ * the sibling must be visited too, and the first leaf hit ends the search.
+ * The hit is the entry into the leaf's capped cylinder; u is the projection of
+ * the hit point onto the leaf axis (App. C).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers unless the call says otherwise; the
+ *    caller owns them.  No entry point keeps a pointer to caller memory after
+ *    it returns.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous and stream-ordered; only fiber_upload, fx_stream_status and
+ *    intersect_closest_host synchronise.
+ *  - Argument errors are reported synchronously, before any launch, and leave
+ *    outputs untouched.  CUDA errors are returned as FX_ECUDA; the message is
+ *    available from fx_last_error().
+ *  - Device-side conditions never trap: they set bits of the handle's sticky
+ *    status word (FX_DEV_*), read and cleared by fx_stream_status.
+ *  - One handle may be used by several calls only in stream order (same
+ *    stream, or streams ordered by events): the persistent kernels share the
+ *    handle's work-queue counters.
+ */
+#ifndef FIBERX_H
+#define FIBERX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FX_OK = 0,
+    FX_EINVAL = -1,       /* bad argument (null pointer, negative size, bad CSR, ...) */
+    FX_ECUDA = -2,        /* a CUDA runtime call failed */
+    FX_ENOMEM = -3,       /* device or host allocation failed */
+    FX_EUNSUPPORTED = -4, /* option not supported */
+    FX_ETIMEOUT = -5,     /* reserved: a bounded device wait ran out */
+    FX_EDEPTH = -6,       /* subdivision depth outside [0, 23] */
+    FX_EDEVICE = -7       /* no usable sm_103 device */
+} fx_status;
+
+/* Sticky device status bits (fx_stream_status). */
+#define FX_DEV_ITER_LIMIT 0x1u  /* a (ray, segment) test hit the per-pair iteration cap */
+#define FX_DEV_UNSUPPORTED 0x2u /* a hit was reported on a piece flagged unsupported */
+#define FX_DEV_BAD_INDEX 0x4u   /* a candidate segment id was out of range (skipped) */
+
+/* intersect_* flags */
+#define FX_KERNEL_PERSISTENT 0x0u /* default: persistent work-queue kernel */
+#define FX_KERNEL_NAIVE 0x1u      /* one thread per (ray, segment) pair (baseline) */
+#define FX_FAST_MATH 0x2u         /* approximate reciprocal / square root in the traversal */
+#define FX_POLISH_FP64 0x4u       /* re-evaluate each hit's leaf in FP64 (intersect_closest) */
+#define FX_COUNT 0x8u             /* accumulate node / descent / backtrack counters */
+#define FX_CHECK_INDEX 0x10u      /* range-check candidate segment ids on the device */
+
+typedef struct fx_fibers fx_fibers; /* opaque; owns the device copy of the fibers */
+
+typedef struct {
+    int32_t max_presplit; /* levels of dyadic pre-split for invalid curves, 0..8 (default 8) */
+    int32_t thick_check;  /* 1 (default): sampled end-plane check for thick fibers (Sec. 3.4) */
+} fx_upload_opts;
+
+typedef struct {
+    int64_t n_seg;         /* segments uploaded */
+    int64_t n_piece;       /* pieces after pre-split (>= n_seg) */
+    int64_t n_presplit;    /* segments split into more than one piece */
+    int64_t n_unsupported; /* pieces still failing the checks at the maximum level */
+    int32_t max_level;     /* deepest pre-split level used */
+    int32_t sm_count;      /* SMs of the device the handle lives on */
+} fx_fibers_info;
+
+/* Launch configuration of the persistent kernels (fx_set_launch). */
+typedef struct {
+    int32_t block;         /* threads per block: 64, 128 or 256 */
+    int32_t blocks_per_sm; /* blocks per SM the grid is sized for (1..16; 0 = as many as fit) */
+    int32_t chunk;         /* rays a warp takes from the queue at a time (1..1024) */
+} fx_launch;
+
+/*
+ * fiber_upload -- validate, pre-split and copy fiber segments to the device.
+ *
+ * cps: n_seg x 4 control points x (x, y, z, r) floats, r >= 0 (Sec. 3.3:
+ * four-dimensional control points, radius interpolated by the Bezier basis).
+ * cps_on_device: 0 = host pointer, 1 = device pointer.  The data is copied;
+ * the caller keeps ownership.  opts may be NULL (defaults).
+ *
+ * Each segment is checked in FP64 against the five inequalities of Sec. 3.4
+ * (App. B.2) and a sampled end-plane check for thick fibers (Sec. 3.4,
+ * Fig. 7); failing curves are halved at u = 1/2 recursively ("subdivided
+ * beforehand", Sec. 3.4) up to max_presplit levels.  A piece at level k is
+ * later traversed to depth d - k, so its leaves coincide with the unsplit
+ * curve's.  Pieces still failing at the last level are kept and counted as
+ * unsupported (not an error).
+ *
+ * Errors: FX_EINVAL (n_seg < 0, null pointers, non-finite values, r < 0),
+ * FX_ENOMEM, FX_ECUDA, FX_EDEVICE.  Synchronises `stream`.
+ */
+fx_status fiber_upload(const float *cps, int64_t n_seg, int32_t cps_on_device,
+                       const fx_upload_opts *opts, void *stream, fx_fibers **out);
+
+/* Releases the handle and its device memory (NULL is a no-op). */
+void fiber_free(fx_fibers *f);
+
+/* Counts describing the uploaded fibers. */
+fx_status fiber_info(const fx_fibers *f, fx_fibers_info *out);
+
+/*
+ * intersect_closest -- closest hit of every ray over its candidate segments.
+ *
+ * rays: n_ray x 8 floats {o.x, o.y, o.z, t_max, w.x, w.y, w.z, 0}; w is
+ * normalised on the device (unit ray, Sec. 3.3); hits need 0 <= t < t_max.
+ * row_ptr: n_ray + 1 int32 (row_ptr[0] = 0, non-decreasing, row_ptr[n_ray] =
+ * n_pair); seg_idx: n_pair int32 segment ids.  The CSR is validated on the
+ * host only for its sizes; set FX_CHECK_INDEX to range-check ids on the
+ * device.
+ * depth: subdivision depth d in [0, 23]; leaves have size 2^-d (Sec. 3.3:
+ * termination after a fixed number of subdivisions).
+ *
+ * Candidates are visited in row order, pieces in order; the closest hit so
+ * far is the t_max of the next test and only a strictly closer hit replaces
+ * it (Sec. 3.2: instant termination; ties keep the earlier candidate).
+ * Outputs per ray: tu (2 floats: t, u in the segment's parameter; miss:
+ * t = +inf, u = -1), seg (int32, -1 on miss), leaf (nullable; int32 start of
+ * the hit leaf in units of 2^-23 of the segment; -1 on miss).
+ * flags: FX_KERNEL_*, FX_FAST_MATH, FX_POLISH_FP64, FX_COUNT, FX_CHECK_INDEX.
+ * Errors: FX_EINVAL, FX_EDEPTH, FX_ECUDA.
+ */
+fx_status intersect_closest(const fx_fibers *f, const float *rays, int64_t n_ray,
+                            const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
+                            int32_t depth, uint32_t flags, float *tu, int32_t *seg,
+                            int32_t *leaf, void *stream);
+
+/*
+ * intersect_pairs -- one result per (ray, candidate) pair, each tested with
+ * the ray's own t_max (no pruning across candidates).  Same inputs as
+ * intersect_closest; outputs per pair: tu (2 floats) and leaf (nullable).
+ * flags: FX_KERNEL_*, FX_FAST_MATH, FX_COUNT, FX_CHECK_INDEX.
+ */
+fx_status intersect_pairs(const fx_fibers *f, const float *rays, int64_t n_ray,
+                          const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
+                          int32_t depth, uint32_t flags, float *tu, int32_t *leaf, void *stream);
+
+/*
+ * intersect_backward -- adjoint of the closest hit's t with respect to the
+ * segments' control points and radii.
+ *
+ * The surface the leaf cylinders converge to (Sec. 3.2) is the sweep of
+ * circles of radius r(u) in the planes normal to c'(u), closed by flat end
+ * disks.  With x = o + t w, a hit satisfies G1 = <x - c(u), c'(u)> = 0 and
+ * G2 = |x - c(u)|^2 - r(u)^2 = 0; (t, u) from the forward pass are refined by
+ * Newton steps on G and dt/dtheta = -[J^-1 dG/dtheta]_t (implicit function
+ * theorem).  End-disk hits (u = 0 or 1) use G1 with u fixed.
+ *
+ * Inputs: rays (as above), tu and seg from intersect_closest, grad_t (n_ray
+ * floats, dL/dt_i).  Output: grad_cps (n_seg x 16 floats, same layout as
+ * cps), ACCUMULATED (+=) with atomics; zero it first for a fresh gradient.
+ * Misses and singular systems (|det J| tiny, grazing) contribute nothing;
+ * their count is added to *n_skipped_dev (device int64, nullable).
+ */
+fx_status intersect_backward(const fx_fibers *f, const float *rays, int64_t n_ray,
+                             const float *tu, const int32_t *seg, const float *grad_t,
+                             float *grad_cps, unsigned long long *n_skipped_dev, void *stream);
+
+/*
+ * intersect_closest_host -- intersect_closest on HOST buffers: copies rays,
+ * row_ptr and seg_idx to device staging owned by the handle, runs, copies
+ * tu / seg / leaf back and synchronises.  Host buffers should be pinned for
+ * full copy bandwidth.  Same flags and errors as intersect_closest, plus
+ * FX_ENOMEM if the staging cannot grow.
+ */
+fx_status intersect_closest_host(fx_fibers *f, const float *rays, int64_t n_ray,
+                                 const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
+                                 int32_t depth, uint32_t flags, float *tu, int32_t *seg,
+                                 int32_t *leaf, void *stream);
+
+/*
+ * fx_set_launch / fx_get_launch -- launch shape of the persistent kernels of
+ * this handle (the autotuner's knobs).  Invalid values give FX_EINVAL.
+ */
+fx_status fx_set_launch(fx_fibers *f, const fx_launch *cfg);
+fx_status fx_get_launch(const fx_fibers *f, fx_launch *cfg);
+
+/*
+ * fx_counters -- node tests, descents, backtracks, pair tests and hits
+ * accumulated by launches with FX_COUNT since the last reset (host array of
+ * 5 uint64; synchronises `stream`).  reset != 0 clears them afterwards.
+ */
+fx_status fx_counters(fx_fibers *f, void *stream, uint64_t *out5, int32_t reset);
+
+/*
+ * fx_stream_status -- synchronises `stream`, returns the handle's sticky
+ * device status bits (FX_DEV_*) in *device_flags and clears them.
+ */
+fx_status fx_stream_status(fx_fibers *f, void *stream, uint32_t *device_flags);
+
+/* Text of the last error on this thread ("" if none). */
+const char *fx_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t fx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIBERX_H */

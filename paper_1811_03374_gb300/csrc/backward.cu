@@ -1,0 +1,158 @@
+// backward.cu -- adjoint of the closest hit's distance t with respect to the
+// segments' control points and radii (hand-written, FP32).
+//
+// The leaf cylinders converge, as the depth grows, to the sweep of circles of
+// radius r(u) in the planes normal to c'(u) (Sec. 3.2: the cylinders' limit
+// surface), closed by flat end disks.  A hit x = o + t w satisfies
+//   G1(t, u) = <x - c(u), c'(u)> = 0,   G2(t, u) = |x - c(u)|^2 - r(u)^2 = 0.
+// The forward (t, u) is refined by Newton steps on G; then the implicit
+// function theorem gives dt/dtheta = -[J^-1 dG/dtheta]_t with
+//   J = [[<w, c'>, <x - c, c''> - |c'|^2], [2 <x - c, w>, -2 <x - c, c'> - 2 r r']],
+//   dG1/dp_k = -B_k c' + B_k' (x - c),  dG2/dp_k = -2 B_k (x - c),
+//   dG2/dr_k = -2 r B_k.
+// End-disk hits (u exactly 0 or 1) keep u fixed and use G1 alone.
+// One thread per ray; contributions are added to grad_cps with atomics.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace fx {
+namespace {
+
+struct V4 {
+  float x, y, z, w;
+};
+
+__device__ __forceinline__ V4 ld(const float4* p) {
+  const float4 v = __ldg(p);
+  return V4{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ float d3(const V4& a, const V4& b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+
+// Exact difference a - b as hi + lo (Knuth's TwoSum).
+__device__ __forceinline__ void two_diff(float a, float b, float& hi, float& lo) {
+  hi = a - b;
+  const float bb = hi - a;
+  lo = (a - (hi - bb)) - (b + bb);
+}
+
+__global__ void __launch_bounds__(256)
+    k_backward(const float4* __restrict__ cp, const float4* __restrict__ rays, int64_t n_ray,
+               const float2* __restrict__ tu, const int32_t* __restrict__ seg,
+               const float* __restrict__ grad_t, float* __restrict__ grad_cps,
+               unsigned long long* n_skipped) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_ray) return;
+  const int32_t s = seg[r];
+  if (s < 0) return;
+  const float gw = grad_t[r];
+  const float4 ra = __ldg(rays + 2 * r), rb = __ldg(rays + 2 * r + 1);
+  const float inv = __frcp_rn(__fsqrt_rn(fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, rb.z * rb.z))));
+  const V4 w{rb.x * inv, rb.y * inv, rb.z * inv, 0.0f};
+  const V4 P0 = ld(cp + 4 * s), P1 = ld(cp + 4 * s + 1), P2 = ld(cp + 4 * s + 2), P3 = ld(cp + 4 * s + 3);
+  // everything relative to p0; o - p0 kept as an exact hi + lo pair
+  V4 oh, ol;
+  two_diff(ra.x, P0.x, oh.x, ol.x);
+  two_diff(ra.y, P0.y, oh.y, ol.y);
+  two_diff(ra.z, P0.z, oh.z, ol.z);
+  // power form around p0: c(u) - p0 = A1 u + A2 u^2 + A3 u^3 (all four components)
+  const V4 D0{P1.x - P0.x, P1.y - P0.y, P1.z - P0.z, P1.w - P0.w};
+  const V4 D1{P2.x - P1.x, P2.y - P1.y, P2.z - P1.z, P2.w - P1.w};
+  const V4 D2{P3.x - P2.x, P3.y - P2.y, P3.z - P2.z, P3.w - P2.w};
+  const V4 A1{3.f * D0.x, 3.f * D0.y, 3.f * D0.z, 3.f * D0.w};
+  const V4 A2{3.f * (D1.x - D0.x), 3.f * (D1.y - D0.y), 3.f * (D1.z - D0.z), 3.f * (D1.w - D0.w)};
+  const V4 A3{D2.x - 2.f * D1.x + D0.x, D2.y - 2.f * D1.y + D0.y, D2.z - 2.f * D1.z + D0.z,
+              D2.w - 2.f * D1.w + D0.w};
+  float t = tu[r].x, u = tu[r].y;
+  const bool cap = (u == 0.0f || u == 1.0f);
+
+  V4 c, c1, c2, e;
+  float J00 = 0.f, J01 = 0.f, J10 = 0.f, J11 = 0.f;
+  auto evaluate = [&](float uu, float tt) {
+    c.x = uu * fmaf(uu, fmaf(uu, A3.x, A2.x), A1.x);
+    c.y = uu * fmaf(uu, fmaf(uu, A3.y, A2.y), A1.y);
+    c.z = uu * fmaf(uu, fmaf(uu, A3.z, A2.z), A1.z);
+    c.w = fmaf(uu, fmaf(uu, fmaf(uu, A3.w, A2.w), A1.w), P0.w);  // r(u)
+    c1.x = fmaf(uu, fmaf(3.f * uu, A3.x, 2.f * A2.x), A1.x);
+    c1.y = fmaf(uu, fmaf(3.f * uu, A3.y, 2.f * A2.y), A1.y);
+    c1.z = fmaf(uu, fmaf(3.f * uu, A3.z, 2.f * A2.z), A1.z);
+    c1.w = fmaf(uu, fmaf(3.f * uu, A3.w, 2.f * A2.w), A1.w);
+    c2.x = fmaf(6.f * uu, A3.x, 2.f * A2.x);
+    c2.y = fmaf(6.f * uu, A3.y, 2.f * A2.y);
+    c2.z = fmaf(6.f * uu, A3.z, 2.f * A2.z);
+    e.x = (fmaf(tt, w.x, oh.x) - c.x) + ol.x;
+    e.y = (fmaf(tt, w.y, oh.y) - c.y) + ol.y;
+    e.z = (fmaf(tt, w.z, oh.z) - c.z) + ol.z;
+    J00 = d3(w, c1);
+    J01 = d3(e, c2) - d3(c1, c1);
+    J10 = 2.f * d3(e, w);
+    J11 = -2.f * d3(e, c1) - 2.f * c.w * c1.w;
+  };
+  bool ok = true;
+  if (!cap) {
+    for (int it = 0; it < 4; ++it) {
+      evaluate(u, t);
+      const float G1 = d3(e, c1), G2 = d3(e, e) - c.w * c.w;
+      const float det = J00 * J11 - J01 * J10;
+      if (!(fabsf(det) > 0.0f)) {
+        ok = false;
+        break;
+      }
+      const float id = __frcp_rn(det);
+      t -= (J11 * G1 - J01 * G2) * id;
+      u -= (J00 * G2 - J10 * G1) * id;
+    }
+    ok = ok && u >= 0.0f && u <= 1.0f && isfinite(t);
+  }
+  evaluate(u, t);
+  float a1 = 0.f, a2 = 0.f;  // dt/dtheta = -(a1 dG1/dtheta + a2 dG2/dtheta)
+  if (cap) {
+    ok = fabsf(J00) > 1e-7f * sqrtf(d3(c1, c1));
+    if (ok) a1 = __frcp_rn(J00);
+  } else if (ok) {
+    const float det = J00 * J11 - J01 * J10;
+    ok = fabsf(det) > 1e-5f * (fabsf(J00 * J11) + fabsf(J01 * J10));
+    if (ok) {
+      const float id = __frcp_rn(det);
+      a1 = J11 * id;
+      a2 = -J01 * id;
+    }
+  }
+  if (!ok) {
+    if (n_skipped) atomicAdd(n_skipped, 1ull);
+    return;
+  }
+  if (gw == 0.0f) return;
+  const float v = 1.0f - u;
+  const float B[4] = {v * v * v, 3.f * u * v * v, 3.f * u * u * v, u * u * u};
+  const float dB[4] = {-3.f * v * v, 3.f * v * v - 6.f * u * v, 6.f * u * v - 3.f * u * u, 3.f * u * u};
+  float* g = grad_cps + 16 * (int64_t)s;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float gx = dB[k] * e.x - B[k] * c1.x, gy = dB[k] * e.y - B[k] * c1.y,
+                gz = dB[k] * e.z - B[k] * c1.z;
+    const float hb = -2.f * B[k];
+    atomicAdd(g + 4 * k + 0, -gw * (a1 * gx + a2 * hb * e.x));
+    atomicAdd(g + 4 * k + 1, -gw * (a1 * gy + a2 * hb * e.y));
+    atomicAdd(g + 4 * k + 2, -gw * (a1 * gz + a2 * hb * e.z));
+    atomicAdd(g + 4 * k + 3, -gw * (a2 * hb * c.w));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const float4* seg_cp, int64_t n_seg, const float4* rays, int64_t n_ray,
+                            const float2* tu, const int32_t* seg, const float* grad_t, float* grad_cps,
+                            unsigned long long* n_skipped, cudaStream_t s) {
+  (void)n_seg;
+  if (n_ray <= 0) return cudaSuccess;
+  const int block = 256;
+  k_backward<<<(unsigned)((n_ray + block - 1) / block), block, 0, s>>>(seg_cp, rays, n_ray, tu, seg, grad_t,
+                                                                       grad_cps, n_skipped);
+  return cudaGetLastError();
+}
+
+}  // namespace fx

@@ -1,0 +1,347 @@
+// fiberx_api.cu -- the C ABI of include/fiberx.h: argument checks, upload,
+// launches and status.  All compute runs in the kernels of trace_kernels.cu
+// and backward.cu; there is no host fallback.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+#include "presplit.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+fx_status fail(fx_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+fx_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return FX_ECUDA;
+}
+
+#define FX_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+unsigned long long* counters_of(const fx_fibers* f) {
+  return reinterpret_cast<unsigned long long*>(f->ws + FX_WS_WORDS);
+}
+
+// Host-side checks shared by the intersect entries; no device access.
+fx_status check_common(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
+                       const int32_t* seg_idx, int64_t n_pair, int32_t depth) {
+  if (!f) return fail(FX_EINVAL, "null fiber handle");
+  if (n_ray < 0 || n_pair < 0) return fail(FX_EINVAL, "negative size");
+  if (n_ray > 0x7fffffffLL || n_pair > 0x7fffffffLL)
+    return fail(FX_EINVAL, "more than 2^31 - 1 rays or pairs");
+  if (depth < 0 || depth > fx::kMaxDepth) return fail(FX_EDEPTH, "depth outside [0, 23]");
+  if (n_ray > 0 && (!rays || !row_ptr)) return fail(FX_EINVAL, "null rays / row_ptr");
+  if (n_pair > 0 && !seg_idx) return fail(FX_EINVAL, "null seg_idx");
+  if (n_ray == 0 && n_pair != 0) return fail(FX_EINVAL, "pairs without rays");
+  return FX_OK;
+}
+
+fx::TraceArgs make_args(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
+                        const int32_t* seg_idx, int64_t n_pair, int32_t depth) {
+  fx::TraceArgs a{};
+  a.piece = f->piece;
+  a.piece_begin = f->piece_begin;
+  a.piece_info = f->piece_info;
+  a.rays = reinterpret_cast<const float4*>(rays);
+  a.row_ptr = row_ptr;
+  a.seg_idx = seg_idx;
+  a.n_ray = n_ray;
+  a.n_pair = n_pair;
+  a.n_seg = (int32_t)f->n_seg;
+  a.depth = depth;
+  a.chunk = f->launch.chunk;
+  a.identity = f->identity ? 1 : 0;
+  a.queue = f->ws + FX_WS_QUEUE;
+  a.status = f->ws + FX_WS_STATUS;
+  a.counters = counters_of(f);
+  return a;
+}
+
+int grid_for(const fx_fibers* f, bool pairs, uint32_t flags) {
+  int per_sm = fx::persistent_occupancy(pairs, flags, f->launch.block);
+  if (per_sm < 1) per_sm = 1;
+  if (f->launch.blocks_per_sm > 0) per_sm = std::min(per_sm, (int)f->launch.blocks_per_sm);
+  return f->sm_count * per_sm;
+}
+
+fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t flags,
+                      cudaStream_t s) {
+  if (a.n_ray == 0) return FX_OK;
+  if (flags & FX_KERNEL_NAIVE) {
+    unsigned long long* scratch = nullptr;
+    if (!pairs) {
+      FX_CUDA(cudaMallocAsync((void**)&scratch, sizeof(unsigned long long) * a.n_ray, s));
+      FX_CUDA(cudaMemsetAsync(scratch, 0xff, sizeof(unsigned long long) * a.n_ray, s));
+    }
+    a.scratch = scratch;
+    cudaError_t e = fx::launch_naive(a, pairs, flags, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "naive kernel launch");
+    return FX_OK;
+  }
+  FX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s));
+  FX_CUDA(fx::launch_persistent(a, pairs, flags, grid_for(f, pairs, flags), f->launch.block, s));
+  return FX_OK;
+}
+
+bool device_is_sm103(int dev, int* sm_count) {
+  cudaDeviceProp p{};
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
+  *sm_count = p.multiProcessorCount;
+  return p.major == 10 && p.minor == 3;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fx_last_error(void) { return g_err.c_str(); }
+
+int32_t fx_version(void) { return 10000; }
+
+fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, const fx_upload_opts* opts,
+                       void* stream, fx_fibers** out) {
+  if (!out) return fail(FX_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n_seg < 0 || n_seg > 0x7ffffffeLL) return fail(FX_EINVAL, "n_seg out of range");
+  if (n_seg > 0 && !cps) return fail(FX_EINVAL, "null control points");
+  const int max_presplit = opts ? opts->max_presplit : 8;
+  const bool thick = opts ? opts->thick_check != 0 : true;
+  if (max_presplit < 0 || max_presplit > 8) return fail(FX_EINVAL, "max_presplit outside [0, 8]");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  int dev = 0, sms = 0;
+  FX_CUDA(cudaGetDevice(&dev));
+  if (!device_is_sm103(dev, &sms)) return fail(FX_EDEVICE, "current device is not sm_103");
+
+  std::vector<float> host((size_t)n_seg * 16);
+  if (n_seg > 0) {
+    if (cps_on_device) {
+      FX_CUDA(cudaMemcpyAsync(host.data(), cps, host.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+      FX_CUDA(cudaStreamSynchronize(s));
+    } else {
+      std::memcpy(host.data(), cps, host.size() * sizeof(float));
+    }
+  }
+  for (int64_t i = 0; i < n_seg; ++i) {
+    for (int k = 0; k < 16; ++k)
+      if (!std::isfinite(host[16 * i + k])) return fail(FX_EINVAL, "non-finite control point");
+    for (int k = 0; k < 4; ++k)
+      if (host[16 * i + 4 * k + 3] < 0.0f) return fail(FX_EINVAL, "negative radius");
+  }
+
+  std::vector<fx::PieceRec> pieces;
+  std::vector<int32_t> begin;
+  const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  fx::presplit_all(host.data(), n_seg, max_presplit, thick, n_seg > 4096 ? nt : 1, pieces, begin);
+
+  fx_fibers* f = new (std::nothrow) fx_fibers();
+  if (!f) return fail(FX_ENOMEM, "handle allocation");
+  f->device = dev;
+  f->sm_count = sms;
+  f->n_seg = n_seg;
+  f->n_piece = (int64_t)pieces.size();
+  std::vector<float> packed(pieces.size() * 16);
+  std::vector<int32_t> info(pieces.size());
+  for (size_t k = 0; k < pieces.size(); ++k) {
+    std::memcpy(&packed[16 * k], pieces[k].pdt, sizeof(pieces[k].pdt));
+    info[k] = pieces[k].level | (pieces[k].off << 4) | (pieces[k].unsupported ? (int32_t)0x80000000 : 0);
+    f->max_level = std::max(f->max_level, pieces[k].level);
+    if (pieces[k].unsupported) f->n_unsupported++;
+    if (pieces[k].level != 0) f->identity = false;
+  }
+  for (int64_t i = 0; i < n_seg; ++i)
+    if (begin[i + 1] - begin[i] > 1) f->n_presplit++;
+
+  auto cleanup = [&](fx_status st, cudaError_t e, const char* where) {
+    fiber_free(f);
+    return e != cudaSuccess ? cuda_fail(e, where) : st;
+  };
+  cudaError_t e;
+  const size_t np = std::max<size_t>(1, pieces.size()), ns = (size_t)std::max<int64_t>(1, n_seg);
+  if ((e = cudaMalloc((void**)&f->piece, np * 64)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc pieces");
+  if ((e = cudaMalloc((void**)&f->piece_begin, (ns + 1) * 4)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc begin");
+  if ((e = cudaMalloc((void**)&f->piece_info, np * 4)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc info");
+  if ((e = cudaMalloc((void**)&f->seg_cp, ns * 64)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc seg_cp");
+  const size_t ws_bytes = FX_WS_WORDS * 4 + 8 * 8;
+  if ((e = cudaMalloc((void**)&f->ws, ws_bytes)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc ws");
+  if ((e = cudaMemsetAsync(f->ws, 0, ws_bytes, s)) != cudaSuccess) return cleanup(FX_ECUDA, e, "memset ws");
+  if (!pieces.empty() &&
+      (e = cudaMemcpyAsync(f->piece, packed.data(), packed.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cleanup(FX_ECUDA, e, "copy pieces");
+  if ((e = cudaMemcpyAsync(f->piece_begin, begin.data(), begin.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cleanup(FX_ECUDA, e, "copy begin");
+  if (!info.empty() &&
+      (e = cudaMemcpyAsync(f->piece_info, info.data(), info.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cleanup(FX_ECUDA, e, "copy info");
+  if (n_seg > 0 &&
+      (e = cudaMemcpyAsync(f->seg_cp, host.data(), host.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cleanup(FX_ECUDA, e, "copy cps");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(FX_ECUDA, e, "upload sync");
+  *out = f;
+  return FX_OK;
+}
+
+void fiber_free(fx_fibers* f) {
+  if (!f) return;
+  cudaFree(f->piece);
+  cudaFree(f->piece_begin);
+  cudaFree(f->piece_info);
+  cudaFree(f->seg_cp);
+  cudaFree(f->ws);
+  cudaFree(f->stage);
+  delete f;
+}
+
+fx_status fiber_info(const fx_fibers* f, fx_fibers_info* out) {
+  if (!f || !out) return fail(FX_EINVAL, "null argument");
+  out->n_seg = f->n_seg;
+  out->n_piece = f->n_piece;
+  out->n_presplit = f->n_presplit;
+  out->n_unsupported = f->n_unsupported;
+  out->max_level = f->max_level;
+  out->sm_count = f->sm_count;
+  return FX_OK;
+}
+
+fx_status fx_set_launch(fx_fibers* f, const fx_launch* cfg) {
+  if (!f || !cfg) return fail(FX_EINVAL, "null argument");
+  const int b = cfg->block;
+  if (!(b == 64 || b == 128 || b == 256)) return fail(FX_EINVAL, "block must be 64, 128 or 256");
+  if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 16) return fail(FX_EINVAL, "blocks_per_sm outside [0, 16]");
+  if (cfg->chunk < 1 || cfg->chunk > 1024) return fail(FX_EINVAL, "chunk outside [1, 1024]");
+  f->launch = *cfg;
+  return FX_OK;
+}
+
+fx_status fx_get_launch(const fx_fibers* f, fx_launch* cfg) {
+  if (!f || !cfg) return fail(FX_EINVAL, "null argument");
+  *cfg = f->launch;
+  return FX_OK;
+}
+
+fx_status intersect_closest(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
+                            const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags, float* tu,
+                            int32_t* seg, int32_t* leaf, void* stream) {
+  fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  if (st != FX_OK) return st;
+  if (n_ray > 0 && (!tu || !seg)) return fail(FX_EINVAL, "null tu / seg output");
+  cudaStream_t s = (cudaStream_t)stream;
+  fx::TraceArgs a = make_args(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  a.tu = reinterpret_cast<float2*>(tu);
+  a.seg = seg;
+  a.leaf = leaf;
+  int32_t* tmp_leaf = nullptr;
+  if ((flags & FX_POLISH_FP64) && !leaf && n_ray > 0) {
+    FX_CUDA(cudaMallocAsync((void**)&tmp_leaf, sizeof(int32_t) * n_ray, s));
+    a.leaf = tmp_leaf;
+  }
+  st = run_forward(f, a, false, flags, s);
+  if (st == FX_OK && (flags & FX_POLISH_FP64)) {
+    cudaError_t e = fx::launch_polish(a, f->seg_cp, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "polish launch");
+  }
+  if (tmp_leaf) cudaFreeAsync(tmp_leaf, s);
+  return st;
+}
+
+fx_status intersect_pairs(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
+                          const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags, float* tu,
+                          int32_t* leaf, void* stream) {
+  fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  if (st != FX_OK) return st;
+  if (n_pair > 0 && !tu) return fail(FX_EINVAL, "null tu output");
+  if (flags & FX_POLISH_FP64) return fail(FX_EUNSUPPORTED, "FP64 polish applies to intersect_closest only");
+  fx::TraceArgs a = make_args(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  a.tu = reinterpret_cast<float2*>(tu);
+  a.leaf = leaf;
+  return run_forward(f, a, true, flags, (cudaStream_t)stream);
+}
+
+fx_status intersect_backward(const fx_fibers* f, const float* rays, int64_t n_ray, const float* tu,
+                             const int32_t* seg, const float* grad_t, float* grad_cps,
+                             unsigned long long* n_skipped_dev, void* stream) {
+  if (!f) return fail(FX_EINVAL, "null fiber handle");
+  if (n_ray < 0 || n_ray > 0x7fffffffLL) return fail(FX_EINVAL, "n_ray out of range");
+  if (n_ray == 0) return FX_OK;
+  if (!rays || !tu || !seg || !grad_t || !grad_cps) return fail(FX_EINVAL, "null argument");
+  FX_CUDA(fx::launch_backward(f->seg_cp, f->n_seg, reinterpret_cast<const float4*>(rays), n_ray,
+                              reinterpret_cast<const float2*>(tu), seg, grad_t, grad_cps, n_skipped_dev,
+                              (cudaStream_t)stream));
+  return FX_OK;
+}
+
+fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
+                                 const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags,
+                                 float* tu, int32_t* seg, int32_t* leaf, void* stream) {
+  fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  if (st != FX_OK) return st;
+  if (n_ray > 0 && (!tu || !seg)) return fail(FX_EINVAL, "null tu / seg output");
+  if (n_ray == 0) return FX_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t b_rays = al((size_t)n_ray * 32), b_rp = al((size_t)(n_ray + 1) * 4),
+               b_si = al((size_t)std::max<int64_t>(n_pair, 1) * 4), b_tu = al((size_t)n_ray * 8),
+               b_seg = al((size_t)n_ray * 4), b_leaf = al((size_t)n_ray * 4);
+  const size_t need = b_rays + b_rp + b_si + b_tu + b_seg + b_leaf;
+  if (need > f->stage_bytes) {
+    FX_CUDA(cudaStreamSynchronize(s));
+    cudaFree(f->stage);
+    f->stage = nullptr;
+    f->stage_bytes = 0;
+    if (cudaMalloc(&f->stage, need) != cudaSuccess) return fail(FX_ENOMEM, "staging allocation");
+    f->stage_bytes = need;
+  }
+  char* base = (char*)f->stage;
+  float* d_rays = (float*)base;
+  int32_t* d_rp = (int32_t*)(base + b_rays);
+  int32_t* d_si = (int32_t*)(base + b_rays + b_rp);
+  float* d_tu = (float*)(base + b_rays + b_rp + b_si);
+  int32_t* d_seg = (int32_t*)(base + b_rays + b_rp + b_si + b_tu);
+  int32_t* d_leaf = (int32_t*)(base + b_rays + b_rp + b_si + b_tu + b_seg);
+  FX_CUDA(cudaMemcpyAsync(d_rays, rays, (size_t)n_ray * 32, cudaMemcpyHostToDevice, s));
+  FX_CUDA(cudaMemcpyAsync(d_rp, row_ptr, (size_t)(n_ray + 1) * 4, cudaMemcpyHostToDevice, s));
+  if (n_pair > 0) FX_CUDA(cudaMemcpyAsync(d_si, seg_idx, (size_t)n_pair * 4, cudaMemcpyHostToDevice, s));
+  st = intersect_closest(f, d_rays, n_ray, d_rp, d_si, n_pair, depth, flags, d_tu, d_seg,
+                         (leaf || (flags & FX_POLISH_FP64)) ? d_leaf : nullptr, stream);
+  if (st != FX_OK) return st;
+  FX_CUDA(cudaMemcpyAsync(tu, d_tu, (size_t)n_ray * 8, cudaMemcpyDeviceToHost, s));
+  FX_CUDA(cudaMemcpyAsync(seg, d_seg, (size_t)n_ray * 4, cudaMemcpyDeviceToHost, s));
+  if (leaf) FX_CUDA(cudaMemcpyAsync(leaf, d_leaf, (size_t)n_ray * 4, cudaMemcpyDeviceToHost, s));
+  FX_CUDA(cudaStreamSynchronize(s));
+  return FX_OK;
+}
+
+fx_status fx_counters(fx_fibers* f, void* stream, uint64_t* out5, int32_t reset) {
+  if (!f || !out5) return fail(FX_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  FX_CUDA(cudaMemcpyAsync(out5, counters_of(f), 5 * 8, cudaMemcpyDeviceToHost, s));
+  if (reset) FX_CUDA(cudaMemsetAsync(counters_of(f), 0, 8 * 8, s));
+  FX_CUDA(cudaStreamSynchronize(s));
+  return FX_OK;
+}
+
+fx_status fx_stream_status(fx_fibers* f, void* stream, uint32_t* device_flags) {
+  if (!f || !device_flags) return fail(FX_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  FX_CUDA(cudaStreamSynchronize(s));
+  FX_CUDA(cudaMemcpy(device_flags, f->ws + FX_WS_STATUS, 4, cudaMemcpyDeviceToHost));
+  FX_CUDA(cudaMemset(f->ws + FX_WS_STATUS, 0, 4));
+  return FX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// internal.h -- host/device shared declarations of the fiberx library (not
+// part of the public C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fiberx.h"
+
+// Workspace words of a handle (device, zeroed at upload).
+enum {
+  FX_WS_QUEUE = 0,    // persistent-kernel ray queue counter (reset before each launch)
+  FX_WS_STATUS = 1,   // sticky FX_DEV_* bits
+  FX_WS_WORDS = 32,   // 128 bytes of uint32 words, then the counters
+};
+
+struct fx_fibers {
+  int device = 0;
+  int sm_count = 0;
+  int64_t n_seg = 0, n_piece = 0, n_presplit = 0, n_unsupported = 0;
+  int32_t max_level = 0;
+  bool identity = true;                 // one level-0 piece per segment
+  float4 *piece = nullptr;              // n_piece x {p, d, t0, t1} world space
+  int32_t *piece_begin = nullptr;       // n_seg + 1
+  int32_t *piece_info = nullptr;        // n_piece: level | off << 4 | unsupported << 31
+  float4 *seg_cp = nullptr;             // n_seg x 4 control points (backward, polish)
+  uint32_t *ws = nullptr;               // FX_WS_WORDS words + 8 uint64 counters
+  fx_launch launch{256, 0, 32};  // blocks_per_sm 0: as many as fit
+  // host-buffer entry staging (grow-only)
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+namespace fx {
+
+constexpr int kMaxDepth = 23;
+
+struct TraceArgs {
+  const float4 *piece;
+  const int32_t *piece_begin;
+  const int32_t *piece_info;
+  const float4 *rays;
+  const int32_t *row_ptr;
+  const int32_t *seg_idx;
+  int64_t n_ray;
+  int64_t n_pair;
+  int32_t n_seg;
+  int32_t depth;
+  int32_t chunk;
+  int32_t identity;
+  float2 *tu;       // per ray (closest) or per pair (pairs)
+  int32_t *seg;     // per ray (closest only)
+  int32_t *leaf;    // nullable
+  uint32_t *queue;
+  uint32_t *status;
+  unsigned long long *counters;  // 5: nodes, descents, backtracks, tests, hits
+  unsigned long long *scratch;   // naive kernel: per-ray packed (t, pair) keys
+};
+
+// Launchers (trace_kernels.cu).  flags: FX_* bits of the public header.
+cudaError_t launch_persistent(const TraceArgs &a, bool pairs, uint32_t flags, int grid, int block,
+                              cudaStream_t s);
+cudaError_t launch_naive(const TraceArgs &a, bool pairs, uint32_t flags, cudaStream_t s);
+cudaError_t launch_polish(const TraceArgs &a, const float4 *seg_cp, cudaStream_t s);
+int persistent_regs(bool pairs, uint32_t flags);
+int persistent_occupancy(bool pairs, uint32_t flags, int block);
+
+// backward.cu
+cudaError_t launch_backward(const float4 *seg_cp, int64_t n_seg, const float4 *rays, int64_t n_ray,
+                            const float2 *tu, const int32_t *seg, const float *grad_t,
+                            float *grad_cps, unsigned long long *n_skipped, cudaStream_t s);
+
+}  // namespace fx

@@ -1,0 +1,660 @@
+// trace_kernels.cu -- forward kernels of the ray / cubic-fiber intersector.
+//
+// k_persistent  persistent work-queue kernel: each warp takes chunks of rays
+//               from an atomic queue; every lane owns one ray, walks its
+//               candidate segments in row order with the closest hit so far
+//               as t_max (Sec. 3.2 instant termination across candidates),
+//               and refills itself from the warp's ray pool (ballot + popc
+//               ranking) the moment its ray is finished, so lanes stay busy
+//               despite uneven candidate counts.  Each loop iteration performs
+//               one node test per lane; the traversal state is the paper's
+//               bit string, start and size in registers (Sec. 3.3).
+// k_naive       one thread per (ray, candidate) pair, same arithmetic; the
+//               closest hit per ray is an atomicMin over packed (t, pair)
+//               keys followed by a resolve pass.  The baseline K1 must beat.
+// k_polish      re-evaluates each hit's leaf cylinder in FP64.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "trace.cuh"
+
+namespace fx {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int iter_cap(int depth) { return 1024 + 64 * depth; }
+
+__device__ __forceinline__ int piece_min_size_shift(int depth, int level) {
+  const int d = depth > level ? depth - level : 0;
+  return 23 - d;
+}
+
+// State of one lane's current (ray, piece) test.
+struct PairState {
+  Node R;      // root node of the piece in the ray frame (for backtracking)
+  Node c;      // current node
+  float tmin, tmax;
+  uint32_t bits, start, size, min_size;
+  int32_t info;  // level | off << 4 | unsupported << 31
+  int32_t iters;
+};
+
+template <bool FAST>
+__device__ __forceinline__ void begin_pair(PairState& st, const TraceArgs& a, int piece,
+                                           const RayFrame& rf, float pair_tmax) {
+  st.R = load_local(a.piece, piece, rf);
+  st.c = st.R;
+  st.bits = 0;
+  st.start = 0;
+  st.size = kRootSize;
+  st.info = a.identity ? 0 : __ldg(a.piece_info + piece);
+  st.min_size = 1u << piece_min_size_shift(a.depth, st.info & 15);
+  st.iters = 0;
+  slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
+}
+
+// Segment-parameter u and leaf start of a piece-local hit.
+__device__ __forceinline__ void to_segment(int32_t info, float u_piece, uint32_t start, float& u,
+                                           int32_t& leaf) {
+  const int lvl = info & 15;
+  const int off = (info >> 4) & 0x7ffff;
+  u = lvl ? ldexpf(__int2float_rn(off) + u_piece, -lvl) : u_piece;
+  leaf = (int32_t)(((uint32_t)off << (23 - lvl)) + (start >> lvl));
+}
+
+// ---------------------------------------------------------------------------
+// persistent kernel
+// ---------------------------------------------------------------------------
+template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
+__global__ void __launch_bounds__(256) k_persistent(const TraceArgs a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  // warp-uniform ray pool
+  int64_t pool_next = 0, pool_end = 0;
+  bool exhausted = false;
+
+  // lane state
+  int64_t ray = -1;
+  int32_t cand = 0, cend = 0, pc = 0, pend = 0, cur_seg = -1, cur_piece = -1;
+  RayFrame rf;
+  float ray_tmax = 0.0f;
+  float best_t = 0.0f, best_u = -1.0f;
+  int32_t best_seg = -1, best_leaf = -1;
+  float cand_t = 0.0f, cand_u = -1.0f;  // PAIRS: best over the current candidate's pieces
+  int32_t cand_leaf = -1;
+  bool active = false;  // a node is ready to be tested
+  bool done = false;    // no more work for this lane
+  PairState st;
+  unsigned long long n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
+
+  for (;;) {
+    // ---- 1. acquire a (ray, piece) pair for every idle lane ---------------
+    bool fresh = false;
+    if (!active && !done) {
+      // advance within the current ray
+      while (ray >= 0) {
+        if (pc < pend) {
+          cur_piece = pc++;
+          fresh = true;
+          break;
+        }
+        if (PAIRS && cand < cend) {
+          a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
+          if (a.leaf) a.leaf[cand] = cand_leaf;
+        }
+        if (++cand < cend) {
+          int32_t s = __ldg(a.seg_idx + cand);
+          if (CHECK && (s < 0 || s >= a.n_seg)) {
+            atomicOr(a.status, FX_DEV_BAD_INDEX);
+            pc = pend = 0;
+            cand_t = kInf;
+            cand_u = -1.0f;
+            cand_leaf = -1;
+            continue;
+          }
+          cur_seg = s;
+          if (a.identity) {
+            pc = s;
+            pend = s + 1;
+          } else {
+            pc = __ldg(a.piece_begin + s);
+            pend = __ldg(a.piece_begin + s + 1);
+          }
+          if (PAIRS) {
+            cand_t = ray_tmax;
+            cand_u = -1.0f;
+            cand_leaf = -1;
+          }
+        } else {
+          if (!PAIRS) {
+            const bool hit = best_seg >= 0;
+            a.tu[ray] = make_float2(hit ? best_t : kInf, hit ? best_u : -1.0f);
+            a.seg[ray] = best_seg;
+            if (a.leaf) a.leaf[ray] = best_leaf;
+          }
+          ray = -1;
+        }
+      }
+    }
+    // lanes without a ray take new rays from the warp pool
+    for (;;) {
+      const bool want = !active && !done && !fresh && ray < 0;
+      const unsigned m = __ballot_sync(kFull, want);
+      if (m == 0u) break;
+      if (pool_next >= pool_end) {
+        if (exhausted) {
+          if (want) done = true;
+          continue;
+        }
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, (unsigned)a.chunk);
+        base = __shfl_sync(kFull, base, 0);
+        if ((int64_t)base >= a.n_ray) {
+          exhausted = true;
+          continue;
+        }
+        pool_next = base;
+        pool_end = min((int64_t)base + a.chunk, a.n_ray);
+      }
+      const int rank = __popc(m & lt_mask);
+      const int64_t avail = pool_end - pool_next;
+      if (want && rank < avail) {
+        ray = pool_next + rank;
+        rf = load_ray<FAST>(a.rays, ray, ray_tmax);
+        best_t = ray_tmax;
+        best_u = -1.0f;
+        best_seg = -1;
+        best_leaf = -1;
+        cand = __ldg(a.row_ptr + ray) - 1;
+        cend = __ldg(a.row_ptr + ray + 1);
+        pc = pend = 0;
+        // walk to the first piece (or finish an empty row)
+        while (ray >= 0) {
+          if (pc < pend) {
+            cur_piece = pc++;
+            fresh = true;
+            break;
+          }
+          if (PAIRS && cand >= 0 && cand < cend && cand >= __ldg(a.row_ptr + ray)) {
+            a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
+            if (a.leaf) a.leaf[cand] = cand_leaf;
+          }
+          if (++cand < cend) {
+            int32_t s = __ldg(a.seg_idx + cand);
+            if (CHECK && (s < 0 || s >= a.n_seg)) {
+              atomicOr(a.status, FX_DEV_BAD_INDEX);
+              pc = pend = 0;
+              cand_t = kInf;
+              cand_u = -1.0f;
+              cand_leaf = -1;
+              continue;
+            }
+            cur_seg = s;
+            if (a.identity) {
+              pc = s;
+              pend = s + 1;
+            } else {
+              pc = __ldg(a.piece_begin + s);
+              pend = __ldg(a.piece_begin + s + 1);
+            }
+            if (PAIRS) {
+              cand_t = ray_tmax;
+              cand_u = -1.0f;
+              cand_leaf = -1;
+            }
+          } else {
+            if (!PAIRS) {
+              a.tu[ray] = make_float2(kInf, -1.0f);
+              a.seg[ray] = -1;
+              if (a.leaf) a.leaf[ray] = -1;
+            }
+            ray = -1;
+          }
+        }
+      }
+      pool_next += min((int64_t)__popc(m), avail);
+    }
+
+    // ---- 2. set up fresh pairs -------------------------------------------
+    if (fresh) {
+      begin_pair<FAST>(st, a, cur_piece, rf, PAIRS ? cand_t : best_t);
+      active = true;
+      if (COUNT) ++n_tests;
+    }
+    if (__all_sync(kFull, !active)) break;
+
+    // ---- 3. node test (Sec. 3.2 / 3.3) ------------------------------------
+    if (active) {
+      const float r = cons_radius<FAST>(st.c);
+      float c0 = 0.0f, c1 = 0.0f;
+      const bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1) &&
+                        fmaxf(c0, st.tmin) <= fminf(c1, st.tmax);
+      if (COUNT) ++n_nodes;
+      ++st.iters;
+      if (over && st.size <= st.min_size) {
+        // leaf: entry into the capped leaf cylinder; stop (instant termination)
+        const float t = fmaxf(c0, st.tmin);
+        const float lim = PAIRS ? cand_t : best_t;
+        if (t < lim) {
+          const float up = leaf_u<FAST>(st.c, t, st.start, st.size);
+          float u;
+          int32_t leaf;
+          to_segment(st.info, up, st.start, u, leaf);
+          if (st.info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
+          if (PAIRS) {
+            cand_t = t;
+            cand_u = u;
+            cand_leaf = leaf;
+          } else {
+            best_t = t;
+            best_u = u;
+            best_seg = cur_seg;
+            best_leaf = leaf;
+          }
+          if (COUNT) ++n_hits;
+        }
+        active = false;
+      } else if (over) {
+        descend<FAST>(st.c, c0, c1, st.tmin, st.tmax, st.bits, st.start, st.size);
+        if (COUNT) ++n_desc;
+      } else if (st.bits == 0u) {
+        active = false;
+      } else {
+        jump_up(st.bits, st.start, st.size);
+        recompute(st.R, st.start, st.size, st.c);
+        slab<FAST>(st.c, PAIRS ? cand_t : best_t, st.tmin, st.tmax);
+        if (COUNT) ++n_back;
+      }
+      if (active && st.iters >= iter_cap(a.depth)) {
+        atomicOr(a.status, FX_DEV_ITER_LIMIT);
+        active = false;
+      }
+    }
+  }
+
+  if (COUNT) {
+    for (int o = 16; o > 0; o >>= 1) {
+      n_nodes += __shfl_down_sync(kFull, n_nodes, o);
+      n_desc += __shfl_down_sync(kFull, n_desc, o);
+      n_back += __shfl_down_sync(kFull, n_back, o);
+      n_tests += __shfl_down_sync(kFull, n_tests, o);
+      n_hits += __shfl_down_sync(kFull, n_hits, o);
+    }
+    if (lane == 0) {
+      atomicAdd(a.counters + 0, n_nodes);
+      atomicAdd(a.counters + 1, n_desc);
+      atomicAdd(a.counters + 2, n_back);
+      atomicAdd(a.counters + 3, n_tests);
+      atomicAdd(a.counters + 4, n_hits);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// naive kernel: one thread per pair
+// ---------------------------------------------------------------------------
+
+// Full traversal of one piece (Sec. 3 / App. C iterative routine).
+template <bool FAST>
+__device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const RayFrame& rf,
+                                            float pair_tmax, float& t_out, float& u_out,
+                                            int32_t& leaf_out, unsigned long long* cnt) {
+  PairState st;
+  begin_pair<FAST>(st, a, piece, rf, pair_tmax);
+  for (;;) {
+    const float r = cons_radius<FAST>(st.c);
+    float c0 = 0.0f, c1 = 0.0f;
+    const bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1) &&
+                      fmaxf(c0, st.tmin) <= fminf(c1, st.tmax);
+    ++st.iters;
+    if (cnt) ++cnt[0];
+    if (over && st.size <= st.min_size) {
+      const float t = fmaxf(c0, st.tmin);
+      if (!(t < pair_tmax)) return false;
+      const float up = leaf_u<FAST>(st.c, t, st.start, st.size);
+      to_segment(st.info, up, st.start, u_out, leaf_out);
+      if (st.info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
+      t_out = t;
+      return true;
+    } else if (over) {
+      descend<FAST>(st.c, c0, c1, st.tmin, st.tmax, st.bits, st.start, st.size);
+      if (cnt) ++cnt[1];
+    } else if (st.bits == 0u) {
+      return false;
+    } else {
+      jump_up(st.bits, st.start, st.size);
+      recompute(st.R, st.start, st.size, st.c);
+      slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
+      if (cnt) ++cnt[2];
+    }
+    if (st.iters >= iter_cap(a.depth)) {
+      atomicOr(a.status, FX_DEV_ITER_LIMIT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t ray_of_pair(const int32_t* __restrict__ row_ptr, int64_t n_ray,
+                                               int64_t j) {
+  // last row r with row_ptr[r] <= j (rows may be empty)
+  int64_t lo = 0, hi = n_ray;  // invariant: row_ptr[lo] <= j < row_ptr[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(row_ptr + mid) <= j) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Closest over the pieces of one candidate, tested with t_max.
+template <bool FAST>
+__device__ __forceinline__ bool trace_candidate(const TraceArgs& a, int32_t s, const RayFrame& rf,
+                                                float tmax, float& t, float& u, int32_t& leaf,
+                                                unsigned long long* cnt) {
+  int pb = s, pe = s + 1;
+  if (!a.identity) {
+    pb = __ldg(a.piece_begin + s);
+    pe = __ldg(a.piece_begin + s + 1);
+  }
+  bool got = false;
+  float lim = tmax;
+  for (int k = pb; k < pe; ++k) {
+    float tk, uk;
+    int32_t lk;
+    if (cnt) ++cnt[3];
+    if (trace_piece<FAST>(a, k, rf, lim, tk, uk, lk, cnt)) {
+      lim = tk;
+      t = tk;
+      u = uk;
+      leaf = lk;
+      got = true;
+    }
+  }
+  return got;
+}
+
+template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
+__global__ void __launch_bounds__(256) k_naive(const TraceArgs a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+  if (j < a.n_pair) {
+    const int64_t r = ray_of_pair(a.row_ptr, a.n_ray, j);
+    float ray_tmax;
+    const RayFrame rf = load_ray<FAST>(a.rays, r, ray_tmax);
+    const int32_t s = __ldg(a.seg_idx + j);
+    float t = kInf, u = -1.0f;
+    int32_t leaf = -1;
+    bool got = false;
+    if (CHECK && (s < 0 || s >= a.n_seg)) {
+      atomicOr(a.status, FX_DEV_BAD_INDEX);
+    } else {
+      got = trace_candidate<FAST>(a, s, rf, ray_tmax, t, u, leaf, COUNT ? cnt : nullptr);
+    }
+    if (COUNT && got) cnt[4] = 1;
+    if (PAIRS) {
+      a.tu[j] = make_float2(got ? t : kInf, got ? u : -1.0f);
+      if (a.leaf) a.leaf[j] = got ? leaf : -1;
+    } else if (got) {
+      // t >= 0, so its bit pattern orders like the value; ties keep the
+      // smaller pair index (the earlier candidate)
+      const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (uint32_t)j;
+      atomicMin(a.scratch + r, key);
+    }
+  }
+  if (COUNT) {
+    for (int k = 0; k < 5; ++k) {
+      unsigned long long v = cnt[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.counters + k, v);
+    }
+  }
+}
+
+// Per ray: decode the winning (t, pair) key and recompute that pair's u/leaf.
+template <bool FAST>
+__global__ void __launch_bounds__(256) k_naive_resolve(const TraceArgs a) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n_ray) return;
+  const unsigned long long key = a.scratch[r];
+  if (key == ~0ull) {
+    a.tu[r] = make_float2(kInf, -1.0f);
+    a.seg[r] = -1;
+    if (a.leaf) a.leaf[r] = -1;
+    return;
+  }
+  const int64_t j = (int64_t)(key & 0xffffffffull);
+  float ray_tmax;
+  const RayFrame rf = load_ray<FAST>(a.rays, r, ray_tmax);
+  const int32_t s = __ldg(a.seg_idx + j);
+  float t = kInf, u = -1.0f;
+  int32_t leaf = -1;
+  trace_candidate<FAST>(a, s, rf, ray_tmax, t, u, leaf, nullptr);
+  a.tu[r] = make_float2(__uint_as_float((uint32_t)(key >> 32)), u);
+  a.seg[r] = s;
+  if (a.leaf) a.leaf[r] = leaf;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 leaf re-evaluation
+// ---------------------------------------------------------------------------
+struct D4 {
+  double x, y, z, w;
+};
+__device__ __forceinline__ double ddot3(const D4& a, const D4& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+// The hit leaf's node recomputed in FP64 from the segment's control points in
+// the ray frame (Sec. 3.3 recomputation), its slab, conservative radius and
+// cylinder (App. A), giving t = max(c0, t_min) and u by projection.
+__global__ void __launch_bounds__(256) k_polish(const TraceArgs a, const float4* __restrict__ cp) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n_ray) return;
+  const int32_t s = a.seg[r];
+  if (s < 0) return;
+  const int32_t leaf = a.leaf[r];
+  // leaf size: 2^-max(depth, level of the piece holding the leaf)
+  int lvl = 0;
+  if (!a.identity) {
+    const int pb = __ldg(a.piece_begin + s), pe = __ldg(a.piece_begin + s + 1);
+    for (int k = pb; k < pe; ++k) {
+      const int32_t info = __ldg(a.piece_info + k);
+      const int kl = info & 15, off = (info >> 4) & 0x7ffff;
+      const int64_t lo = (int64_t)off << (23 - kl), hi = (int64_t)(off + 1) << (23 - kl);
+      if (leaf >= lo && leaf < hi) {
+        lvl = kl;
+        break;
+      }
+    }
+  }
+  const int dl = a.depth > lvl ? a.depth : lvl;
+  const double size = (double)(1u << (23 - dl)) * (1.0 / 8388608.0);
+  const double u0 = (double)leaf * (1.0 / 8388608.0), u1 = u0 + size;
+  // ray frame in FP64 (Gram-Schmidt; any orthonormal frame gives the same result)
+  const float4 ra = a.rays[2 * r], rb = a.rays[2 * r + 1];
+  double w[3] = {rb.x, rb.y, rb.z};
+  const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  w[0] /= wn; w[1] /= wn; w[2] /= wn;
+  double e1[3], e2[3];
+  {
+    const double s0 = copysign(1.0, w[2]);
+    const double aa = -1.0 / (s0 + w[2]);
+    const double bb = w[0] * w[1] * aa;
+    e1[0] = 1.0 + s0 * w[0] * w[0] * aa; e1[1] = s0 * bb; e1[2] = -s0 * w[0];
+    e2[0] = bb; e2[1] = s0 + w[1] * w[1] * aa; e2[2] = -w[1];
+  }
+  D4 Q[4];
+  for (int k = 0; k < 4; ++k) {
+    const float4 P = cp[4 * s + k];
+    const double q0 = (double)P.x - ra.x, q1 = (double)P.y - ra.y, q2 = (double)P.z - ra.z;
+    Q[k].x = q0 * e1[0] + q1 * e1[1] + q2 * e1[2];
+    Q[k].y = q0 * e2[0] + q1 * e2[1] + q2 * e2[2];
+    Q[k].z = q0 * w[0] + q1 * w[1] + q2 * w[2];
+    Q[k].w = P.w;
+  }
+  auto eval = [&](double u) {
+    const double v = 1.0 - u, b0 = v * v * v, b1 = 3 * u * v * v, b2 = 3 * u * u * v, b3 = u * u * u;
+    return D4{b0 * Q[0].x + b1 * Q[1].x + b2 * Q[2].x + b3 * Q[3].x,
+              b0 * Q[0].y + b1 * Q[1].y + b2 * Q[2].y + b3 * Q[3].y,
+              b0 * Q[0].z + b1 * Q[1].z + b2 * Q[2].z + b3 * Q[3].z,
+              b0 * Q[0].w + b1 * Q[1].w + b2 * Q[2].w + b3 * Q[3].w};
+  };
+  auto deriv3 = [&](double u) {
+    const double v = 1.0 - u, b0 = v * v, b1 = 2 * u * v, b2 = u * u;
+    return D4{b0 * (Q[1].x - Q[0].x) + b1 * (Q[2].x - Q[1].x) + b2 * (Q[3].x - Q[2].x),
+              b0 * (Q[1].y - Q[0].y) + b1 * (Q[2].y - Q[1].y) + b2 * (Q[3].y - Q[2].y),
+              b0 * (Q[1].z - Q[0].z) + b1 * (Q[2].z - Q[1].z) + b2 * (Q[3].z - Q[2].z),
+              b0 * (Q[1].w - Q[0].w) + b1 * (Q[2].w - Q[1].w) + b2 * (Q[3].w - Q[2].w)};
+  };
+  const D4 cp0 = eval(u0), cp1 = eval(u1), g0 = deriv3(u0), g1 = deriv3(u1);
+  const D4 p = cp0;
+  const D4 d{cp1.x - cp0.x, cp1.y - cp0.y, cp1.z - cp0.z, cp1.w - cp0.w};
+  const D4 t0{size * g0.x, size * g0.y, size * g0.z, size * g0.w};
+  const D4 t1{size * g1.x, size * g1.y, size * g1.z, size * g1.w};
+  // slab
+  double lo = 0.0, hi = ra.w;
+  if (t0.z != 0.0) {
+    const double t = ddot3(t0, p) / t0.z;
+    if (t0.z > 0.0) lo = fmax(lo, t); else hi = fmin(hi, t);
+  } else if (ddot3(t0, p) > 0.0) {
+    lo = 1e300;
+  }
+  const D4 q{p.x + d.x, p.y + d.y, p.z + d.z, 0.0};
+  if (t1.z != 0.0) {
+    const double t = ddot3(t1, q) / t1.z;
+    if (t1.z < 0.0) lo = fmax(lo, t); else hi = fmin(hi, t);
+  } else if (ddot3(t1, q) < 0.0) {
+    lo = 1e300;
+  }
+  // conservative radius
+  const double dd = ddot3(d, d);
+  double m;
+  if (dd > 0.0) {
+    const double b0 = ddot3(t0, d) / dd, b1 = ddot3(t1, d) / dd;
+    const double qx = t0.x - b0 * d.x, qy = t0.y - b0 * d.y, qz = t0.z - b0 * d.z;
+    const double sx = t1.x - b1 * d.x, sy = t1.y - b1 * d.y, sz = t1.z - b1 * d.z;
+    m = fmax(qx * qx + qy * qy + qz * qz, sx * sx + sy * sy + sz * sz);
+  } else {
+    m = fmax(ddot3(t0, t0), ddot3(t1, t1));
+  }
+  const double rad = sqrt(m) + p.w + fmax(fmax(0.0, t0.w), fmax(d.w, d.w - t1.w));
+  // cylinder
+  const double g = d.x * d.x + d.y * d.y;
+  double c0, c1;
+  if (g == 0.0) {
+    if (!(p.x * p.x + p.y * p.y < rad * rad)) return;
+    c0 = -1e300;
+    c1 = 1e300;
+  } else {
+    const double cr = d.x * p.y - d.y * p.x;
+    const double e = rad * rad - cr * cr / g;
+    if (e < 0.0) return;  // FP32 and FP64 disagree on the leaf: keep the FP32 value
+    const double tcpa = p.z - d.z * (d.x * p.x + d.y * p.y) / g;
+    const double sq = sqrt(e * (d.z * d.z + g) / g);
+    c0 = tcpa - sq;
+    c1 = tcpa + sq;
+  }
+  if (!(fmax(c0, lo) <= fmin(c1, hi))) return;
+  const double t = fmax(c0, lo);
+  double ul = 0.0;
+  if (dd > 0.0) ul = fmin(1.0, fmax(0.0, (-p.x * d.x - p.y * d.y + (t - p.z) * d.z) / dd));
+  a.tu[r] = make_float2((float)t, (float)(u0 + ul * size));
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
+static cudaError_t launch_p(const TraceArgs& a, int grid, int block, cudaStream_t s) {
+  k_persistent<FAST, PAIRS, COUNT, CHECK><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool FAST, bool PAIRS>
+static cudaError_t launch_p2(const TraceArgs& a, uint32_t flags, int grid, int block,
+                             cudaStream_t s) {
+  const bool cnt = flags & FX_COUNT, chk = flags & FX_CHECK_INDEX;
+  if (cnt) return chk ? launch_p<FAST, PAIRS, true, true>(a, grid, block, s)
+                      : launch_p<FAST, PAIRS, true, false>(a, grid, block, s);
+  return chk ? launch_p<FAST, PAIRS, false, true>(a, grid, block, s)
+             : launch_p<FAST, PAIRS, false, false>(a, grid, block, s);
+}
+
+cudaError_t launch_persistent(const TraceArgs& a, bool pairs, uint32_t flags, int grid, int block,
+                              cudaStream_t s) {
+  const bool fast = flags & FX_FAST_MATH;
+  if (pairs) return fast ? launch_p2<true, true>(a, flags, grid, block, s)
+                         : launch_p2<false, true>(a, flags, grid, block, s);
+  return fast ? launch_p2<true, false>(a, flags, grid, block, s)
+              : launch_p2<false, false>(a, flags, grid, block, s);
+}
+
+int persistent_regs(bool pairs, uint32_t flags) {
+  cudaFuncAttributes at{};
+  const bool fast = flags & FX_FAST_MATH;
+  cudaError_t e;
+  if (pairs) e = fast ? cudaFuncGetAttributes(&at, k_persistent<true, true, false, false>)
+                      : cudaFuncGetAttributes(&at, k_persistent<false, true, false, false>);
+  else e = fast ? cudaFuncGetAttributes(&at, k_persistent<true, false, false, false>)
+                : cudaFuncGetAttributes(&at, k_persistent<false, false, false, false>);
+  return e == cudaSuccess ? at.numRegs : -1;
+}
+
+int persistent_occupancy(bool pairs, uint32_t flags, int block) {
+  int n = 0;
+  const bool fast = flags & FX_FAST_MATH, cnt = flags & FX_COUNT, chk = flags & FX_CHECK_INDEX;
+  // occupancy of the instantiation that will be launched
+#define FX_OCC(F, P, C, K) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<F, P, C, K>, block, 0)
+  cudaError_t e;
+  if (pairs) {
+    if (fast) e = cnt ? (chk ? FX_OCC(true, true, true, true) : FX_OCC(true, true, true, false))
+                      : (chk ? FX_OCC(true, true, false, true) : FX_OCC(true, true, false, false));
+    else e = cnt ? (chk ? FX_OCC(false, true, true, true) : FX_OCC(false, true, true, false))
+                 : (chk ? FX_OCC(false, true, false, true) : FX_OCC(false, true, false, false));
+  } else {
+    if (fast) e = cnt ? (chk ? FX_OCC(true, false, true, true) : FX_OCC(true, false, true, false))
+                      : (chk ? FX_OCC(true, false, false, true) : FX_OCC(true, false, false, false));
+    else e = cnt ? (chk ? FX_OCC(false, false, true, true) : FX_OCC(false, false, true, false))
+                 : (chk ? FX_OCC(false, false, false, true) : FX_OCC(false, false, false, false));
+  }
+#undef FX_OCC
+  return e == cudaSuccess ? n : 0;
+}
+
+template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
+static cudaError_t launch_n(const TraceArgs& a, cudaStream_t s) {
+  const int block = 256;
+  if (a.n_pair > 0) {
+    const int64_t grid = (a.n_pair + block - 1) / block;
+    k_naive<FAST, PAIRS, COUNT, CHECK><<<(unsigned)grid, block, 0, s>>>(a);
+  }
+  if (!PAIRS && a.n_ray > 0) {
+    k_naive_resolve<FAST><<<(unsigned)((a.n_ray + block - 1) / block), block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <bool FAST, bool PAIRS>
+static cudaError_t launch_n2(const TraceArgs& a, uint32_t flags, cudaStream_t s) {
+  const bool cnt = flags & FX_COUNT, chk = flags & FX_CHECK_INDEX;
+  if (cnt) return chk ? launch_n<FAST, PAIRS, true, true>(a, s) : launch_n<FAST, PAIRS, true, false>(a, s);
+  return chk ? launch_n<FAST, PAIRS, false, true>(a, s) : launch_n<FAST, PAIRS, false, false>(a, s);
+}
+
+cudaError_t launch_naive(const TraceArgs& a, bool pairs, uint32_t flags, cudaStream_t s) {
+  const bool fast = flags & FX_FAST_MATH;
+  if (pairs) return fast ? launch_n2<true, true>(a, flags, s) : launch_n2<false, true>(a, flags, s);
+  return fast ? launch_n2<true, false>(a, flags, s) : launch_n2<false, false>(a, flags, s);
+}
+
+cudaError_t launch_polish(const TraceArgs& a, const float4* seg_cp, cudaStream_t s) {
+  if (a.n_ray > 0) {
+    const int block = 256;
+    k_polish<<<(unsigned)((a.n_ray + block - 1) / block), block, 0, s>>>(a, seg_cp);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fx

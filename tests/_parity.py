@@ -1,0 +1,119 @@
+"""Element-wise comparison of the CUDA path with the FP64 oracle.
+
+A ray passes when hit/miss agree and, for hits, the segment is the same,
+|t - t_ref| <= TOL_T * t_ref and |u - u_ref| <= TOL_U (the stated tolerance:
+relative t error <= 1e-5, |u error| <= 1e-5).
+
+Rays that fail this strict rule are re-run through the oracle with the ray
+shifted sideways (8 directions orthogonal to it) by the resolution band
+    delta = 1e-4 r + 8 * 2^-24 * (|o| + t):
+1e-4 r is the silhouette band within which hit/miss may differ, the second
+term is the spacing of FP32 coordinates along the ray, below which no FP32
+computation can resolve a decision (a silhouette, a split plane, an end
+plane).  A ray passes "in band" if the oracle result for one shifted copy
+meets the strict rule; every other ray is a failure.
+"""
+import numpy as np
+
+import oracle as O
+
+TOL_T = 1e-5
+TOL_U = 1e-5
+EPS32 = 2.0 ** -24
+
+
+def strict_ok(t_g, u_g, s_g, t_o, u_o, s_o):
+    hit_g, hit_o = s_g >= 0, s_o >= 0
+    ok = hit_g == hit_o
+    both = hit_g & hit_o
+    with np.errstate(invalid="ignore"):
+        vals = (s_g == s_o) & (np.abs(t_g - t_o) <= TOL_T * np.abs(t_o)) & (np.abs(u_g - u_o) <= TOL_U)
+    return ok & (~both | vals)
+
+
+def _radius_at(cps, seg, u):
+    cp = cps[seg].astype(np.float64)
+    u = np.clip(u, 0, 1)[:, None]
+    v = 1 - u
+    B = np.concatenate([v ** 3, 3 * u * v * v, 3 * u * u * v, u ** 3], axis=1)
+    return np.sum(B * cp[:, :, 3], axis=1)
+
+
+def _perp(w):
+    a = np.where(np.abs(w[:, :1]) < 0.9, np.array([[1.0, 0, 0]]), np.array([[0.0, 1, 0]]))
+    e1 = a - np.sum(a * w, axis=1, keepdims=True) * w
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(w, e1)
+    return e1, e2
+
+
+def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
+    """Indices (subset of idx) whose GPU result the oracle reproduces for a
+    sideways-shifted copy of the ray."""
+    if len(idx) == 0:
+        return np.zeros(0, dtype=np.int64)
+    rays = case["rays"][idx].astype(np.float64)
+    o, w = rays[:, :3], rays[:, 4:7]
+    w = w / np.linalg.norm(w, axis=1, keepdims=True)
+    t_ref = np.where(np.isfinite(t_g[idx]), t_g[idx], 0.0)
+    seg = np.where(s_g[idx] >= 0, s_g[idx], 0)
+    r = _radius_at(case["cps"], seg, u_g[idx])
+    r = np.where(s_g[idx] >= 0, r, case["cps"][:, :, 3].max())
+    delta = 1e-4 * r + 8 * EPS32 * (np.linalg.norm(o, axis=1) + t_ref)
+    e1, e2 = _perp(w)
+    dirs = [e1, -e1, e2, -e2, (e1 + e2) / np.sqrt(2), (e1 - e2) / np.sqrt(2),
+            (-e1 + e2) / np.sqrt(2), (-e1 - e2) / np.sqrt(2)]
+    rp = case["row_ptr"].astype(np.int64)
+    sub_rays, rows, segs = [], [0], []
+    for k, dvec in enumerate(dirs):
+        rr = case["rays"][idx].copy()
+        rr[:, :3] = (o + delta[:, None] * dvec).astype(np.float32)
+        sub_rays.append(rr)
+    for k in range(len(dirs)):
+        for i in idx:
+            cand = case["seg_idx"][rp[i]:rp[i + 1]]
+            segs.append(cand)
+            rows.append(rows[-1] + len(cand))
+    sub = dict(cps=case["cps"], rays=np.concatenate(sub_rays),
+               row_ptr=np.array(rows, dtype=np.int32),
+               seg_idx=np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32))
+    ref = O.closest(sub, depth, pieces)
+    m = len(idx)
+    ok = np.zeros(m, dtype=bool)
+    for k in range(len(dirs)):
+        sl = slice(k * m, (k + 1) * m)
+        ok |= strict_ok(t_g[idx], u_g[idx], s_g[idx], ref["t"][sl], ref["u"][sl], ref["seg"][sl])
+    return idx[ok]
+
+
+def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces):
+    """Returns a stats dict; 'fail' lists ray indices failing strict and band."""
+    t_g = gpu_tu[:, 0].astype(np.float64)
+    u_g = gpu_tu[:, 1].astype(np.float64)
+    s_g = gpu_seg.astype(np.int64)
+    ok = strict_ok(t_g, u_g, s_g, ref["t"], ref["u"], ref["seg"].astype(np.int64))
+    bad = np.nonzero(~ok)[0]
+    banded = band_check(case, bad, t_g, u_g, s_g, depth, pieces)
+    fail = np.setdiff1d(bad, banded)
+    both = (s_g >= 0) & (ref["seg"] >= 0) & ok
+    rel = np.abs(t_g[both] - ref["t"][both]) / ref["t"][both] if both.any() else np.zeros(1)
+    du = np.abs(u_g[both] - ref["u"][both]) if both.any() else np.zeros(1)
+    return dict(n=len(s_g), hits=int((ref["seg"] >= 0).sum()), strict=int(ok.sum()),
+                band=int(len(banded)), fail=fail, max_rel_t=float(rel.max()), max_du=float(du.max()),
+                med_rel_t=float(np.median(rel)))
+
+
+def pairs_min(pr, case):
+    """Closest per ray from per-pair oracle hits (ties: earlier candidate)."""
+    rp = case["row_ptr"].astype(np.int64)
+    n = len(rp) - 1
+    t = np.full(n, np.inf)
+    u = np.full(n, -1.0)
+    s = np.full(n, -1, dtype=np.int64)
+    for i in range(n):
+        a, b = rp[i], rp[i + 1]
+        if b > a:
+            j = a + int(np.argmin(pr["t"][a:b]))
+            if np.isfinite(pr["t"][j]):
+                t[i], u[i], s[i] = pr["t"][j], pr["u"][j], case["seg_idx"][j]
+    return dict(t=t, u=u, seg=s)

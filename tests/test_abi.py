@@ -1,0 +1,62 @@
+"""The C ABI library builds, loads and exports every function include/fiberx.h
+declares; host-side argument checks answer with the documented codes without
+touching a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1811_03374_gb300 import fiberx as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fiberx.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_binding_exports():
+    assert sorted(F.EXPORTS) == declared_functions()
+
+
+def test_library_exports_every_declared_symbol():
+    L = F.lib()
+    assert os.path.dirname(F.library_path()).startswith(ROOT)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert L.fx_version() == 10000
+
+
+def test_argument_errors_without_device():
+    L = F.lib()
+    h = ctypes.c_void_p()
+    # negative segment count and null output are rejected before any CUDA call
+    assert L.fiber_upload(None, -1, 0, None, None, ctypes.byref(h)) == -1
+    assert L.fiber_upload(None, 1, 0, None, None, None) == -1
+    assert L.fiber_upload(None, 4, 0, None, None, ctypes.byref(h)) == -1
+    opts = F.UploadOpts(9, 1)
+    assert L.fiber_upload(None, 0, 0, ctypes.byref(opts), None, ctypes.byref(h)) == -1
+    # null handle
+    assert L.intersect_closest(None, None, 0, None, None, 0, 8, 0, None, None, None, None) == -1
+    assert L.intersect_pairs(None, None, 0, None, None, 0, 8, 0, None, None, None) == -1
+    assert L.intersect_backward(None, None, 0, None, None, None, None, None, None) == -1
+    assert L.fiber_info(None, None) == -1
+    assert L.fx_stream_status(None, None, None) == -1
+    assert b"null" in L.fx_last_error()
+    L.fiber_free(None)  # no-op
+
+
+def test_python_binding_has_no_cpu_fallback():
+    # without a CUDA device the binding must fail loudly, never compute
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1811_03374_gb300 import inputs
+    case = inputs.tiny_case(n_ray=4)
+    with pytest.raises(Exception):
+        F.Fibers(case["cps"])

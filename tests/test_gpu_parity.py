@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by
+element on seeded inputs: the tiny workload at depth 8, the depth sweep 2..22
+on three curvature classes, the hair patch at full size (sampled rays), the
+per-pair and naive kernels, the FP64 polish, counters and edge cases."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_03374_gb300 import fiberx as F
+from paper_1811_03374_gb300 import inputs as I
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _np(x):
+    return x.cpu().numpy()
+
+
+def _run_closest(case, depth, flags=0, fib=None):
+    own = fib is None
+    if own:
+        fib = F.Fibers(case["cps"])
+    tu, seg, leaf = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth, flags)
+    torch.cuda.synchronize()
+    st = fib.status()
+    if own:
+        fib.close()
+    return _np(tu), _np(seg), _np(leaf), st
+
+
+def _assert_parity(stats, max_band_frac=5e-3):
+    assert len(stats["fail"]) == 0, "rays failing parity: %s" % stats["fail"][:10]
+    assert stats["band"] <= max_band_frac * max(stats["n"], 1), stats
+    assert stats["max_rel_t"] <= P.TOL_T and stats["max_du"] <= P.TOL_U
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    case = I.tiny_case()
+    pieces = O.presplit(case["cps"])
+    ref = O.closest(case, 8, pieces)
+    return case, pieces, ref
+
+
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+def test_tiny_closest_persistent(tiny, flags):
+    case, pieces, ref = tiny
+    tu, seg, leaf, st = _run_closest(case, 8, flags)
+    assert st == 0
+    stats = P.compare_closest(case, 8, tu, seg, ref, pieces)
+    _assert_parity(stats)
+    assert stats["hits"] > 3000
+    strict = P.strict_ok(tu[:, 0], tu[:, 1], seg, ref["t"], ref["u"], ref["seg"])
+    same = strict & (seg >= 0)
+    assert np.mean(leaf[same] == ref["leaf"][same]) > 0.999
+
+
+def test_tiny_closest_naive(tiny):
+    case, pieces, _ = tiny
+    pr = O.pairs(case, 8, pieces)
+    ref = P.pairs_min(pr, case)
+    tu, seg, leaf, st = _run_closest(case, 8, F.FX_KERNEL_NAIVE)
+    assert st == 0
+    _assert_parity(P.compare_closest(case, 8, tu, seg, ref, pieces))
+
+
+@pytest.mark.parametrize("kernel", [F.FX_KERNEL_PERSISTENT, F.FX_KERNEL_NAIVE], ids=["persistent", "naive"])
+def test_tiny_pairs(tiny, kernel):
+    case, pieces, _ = tiny
+    sub = I.subsample_rays(case, np.arange(0, 16384, 4))
+    pr = O.pairs(sub, 8, pieces)
+    fib = F.Fibers(sub["cps"])
+    tu, leaf = F.intersect_pairs(fib, sub["rays"], sub["row_ptr"], sub["seg_idx"], 8, kernel)
+    tu = _np(tu)
+    assert fib.status() == 0
+    fib.close()
+    hit_g, hit_o = np.isfinite(tu[:, 0]), np.isfinite(pr["t"])
+    agree = hit_g == hit_o
+    both = hit_g & hit_o
+    rel = np.abs(tu[both, 0] - pr["t"][both]) / pr["t"][both]
+    du = np.abs(tu[both, 1] - pr["u"][both])
+    assert agree.mean() > 0.999
+    assert np.mean((rel <= P.TOL_T) & (du <= P.TOL_U)) > 0.999
+    assert both.sum() > 1000
+
+
+def test_presplit_counts_match_oracle(tiny):
+    case, pieces, _ = tiny
+    fib = F.Fibers(case["cps"])
+    info = fib.info()
+    fib.close()
+    counts = np.diff(pieces["begin"])
+    assert info["n_seg"] == 16
+    assert info["n_piece"] == len(pieces["seg"])
+    assert info["n_presplit"] == int((counts > 1).sum())
+    assert info["n_unsupported"] == int(pieces["flags"].sum())
+    assert info["max_level"] == int(pieces["level"].max())
+
+
+DEPTHS = [2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 18, 20, 22]
+
+
+@pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
+@pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
+def test_depth_sweep(klass, forced):
+    case = I.sweep_case(klass, 4096, forced_hits=forced)
+    pieces = O.presplit(case["cps"])
+    fib = F.Fibers(case["cps"])
+    worst = 0.0
+    for depth in DEPTHS:
+        ref = O.closest(case, depth, pieces)
+        tu, seg, leaf, _ = _run_closest(case, depth, 0, fib)
+        stats = P.compare_closest(case, depth, tu, seg, ref, pieces)
+        _assert_parity(stats)
+        worst = max(worst, stats["max_rel_t"])
+        if forced:
+            assert stats["hits"] > 3500
+    assert fib.status() == 0
+    fib.close()
+
+
+def test_counters_match_oracle(tiny):
+    case, pieces, ref = tiny
+    fib = F.Fibers(case["cps"])
+    fib.counters(reset=True)
+    F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8, F.FX_COUNT)
+    c = fib.counters(reset=True)
+    fib.close()
+    oc = ref["counters"]
+    assert c["tests"] == oc["tests"]
+    for k in ("nodes", "descents", "backtracks", "hits"):
+        assert abs(c[k] - oc[k]) <= 1e-3 * oc[k] + 2, (k, c[k], oc[k])
+
+
+def test_polish_fp64_matches_oracle_leaf():
+    case = I.sweep_case("moderate", 4096, forced_hits=True)
+    pieces = O.presplit(case["cps"])
+    fib = F.Fibers(case["cps"])
+    for depth in (4, 12, 20):
+        tu, seg, leaf, _ = _run_closest(case, depth, F.FX_POLISH_FP64, fib)
+        ok = seg >= 0
+        ref_t = np.full(len(seg), np.nan)
+        for i in np.nonzero(ok)[0][:400]:
+            r7 = O.ray7_from_packed(case["rays"][i])
+            lh = O.leaf_hit(r7, case["cps"][seg[i]].astype(np.float64), depth, leaf[i] >> (23 - depth))
+            if lh is not None:
+                ref_t[i] = lh[0]
+        m = np.isfinite(ref_t)
+        assert m.sum() > 300
+        rel = np.abs(tu[m, 0] - ref_t[m]) / ref_t[m]
+        assert rel.max() < 2e-7  # FP64 value rounded once to FP32
+    fib.close()
+
+
+def test_host_entry_matches_device(tiny):
+    case, _, _ = tiny
+    fib = F.Fibers(case["cps"])
+    tu_d, seg_d, leaf_d = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8)
+    tu_h, seg_h, leaf_h = F.intersect_closest_host(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8)
+    np.testing.assert_array_equal(_np(tu_d), tu_h.numpy())
+    np.testing.assert_array_equal(_np(seg_d), seg_h.numpy())
+    np.testing.assert_array_equal(_np(leaf_d), leaf_h.numpy())
+    fib.close()
+
+
+def test_edge_cases():
+    case = I.sweep_case("moderate", 64, forced_hits=True)
+    fib = F.Fibers(case["cps"])
+    # no rays
+    tu, seg, _ = F.intersect_closest(fib, np.zeros((0, 8), np.float32), np.zeros(1, np.int32),
+                                     np.zeros(0, np.int32), 8)
+    assert tu.shape == (0, 2)
+    # rays without candidates, and a ray listing every segment
+    rp = np.array([0, 0, 0, 64, 64], dtype=np.int32)
+    rays = case["rays"][:4].copy()
+    si = np.arange(64, dtype=np.int32)
+    tu, seg, _ = F.intersect_closest(fib, rays, rp, si, 8)
+    seg = _np(seg)
+    assert seg[0] == -1 and seg[1] == -1 and seg[3] == -1
+    sub = dict(cps=case["cps"], rays=rays, row_ptr=rp, seg_idx=si)
+    ref = O.closest(sub, 8)
+    assert seg[2] == ref["seg"][2]
+    # finite t_max removes hits beyond it
+    tu0, seg0, _ = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8)
+    r2 = case["rays"].copy()
+    r2[:, 3] = 0.5 * _np(tu0)[:, 0].clip(0, 100)
+    tu1, seg1, _ = F.intersect_closest(fib, r2, case["row_ptr"], case["seg_idx"], 8)
+    assert np.all(_np(seg1) == -1)
+    # depth 0 (single cylinder) and 23 (finest)
+    for d in (0, 23):
+        ref = O.closest(case, d)
+        tu, seg, _, _ = _run_closest(case, d, 0, fib)
+        stats = P.compare_closest(case, d, tu, seg, ref, O.presplit(case["cps"]))
+        _assert_parity(stats, max_band_frac=0.05)
+    # bad depth and bad sizes are refused before launch
+    with pytest.raises(F.FiberxError):
+        F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 24)
+    with pytest.raises(F.FiberxError):
+        F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], -1)
+    # out-of-range segment ids are skipped and flagged when checking is on
+    bad = case["seg_idx"].copy()
+    bad[5] = 10_000
+    tu, seg, _ = F.intersect_closest(fib, case["rays"], case["row_ptr"], bad, 8, F.FX_CHECK_INDEX)
+    assert _np(seg)[5] == -1
+    assert fib.status() & F.FX_DEV_BAD_INDEX
+    assert fib.status() == 0  # cleared by the read
+    fib.close()
+
+
+def test_upload_rejects_bad_fibers():
+    cps = I.tiny_case(n_ray=1)["cps"].copy()
+    cps[3, 2, 3] = -0.1
+    with pytest.raises(F.FiberxError):
+        F.Fibers(cps)
+    cps[3, 2, 3] = np.nan
+    with pytest.raises(F.FiberxError):
+        F.Fibers(cps)
+    empty = F.Fibers(np.zeros((0, 4, 4), np.float32))
+    assert empty.info()["n_piece"] == 0
+    empty.close()
+
+
+@pytest.fixture(scope="module")
+def hair():
+    return I.hair_patch()
+
+
+def test_hair_patch_full_size_sampled(hair):
+    # the benchmark's workload and launch: full frame on the GPU, oracle on a
+    # seeded sample of rays that have candidates
+    case = hair
+    depth = 10
+    tu, seg, leaf, st = _run_closest(case, depth)
+    assert st == 0
+    counts = np.diff(case["row_ptr"])
+    g = np.random.default_rng(5)
+    idx = np.sort(g.choice(np.nonzero(counts > 0)[0], 3000, replace=False))
+    sub = I.subsample_rays(case, idx)
+    pieces = O.presplit(case["cps"])
+    ref = O.closest(sub, depth, pieces)
+    stats = P.compare_closest(sub, depth, tu[idx], seg[idx], ref, pieces)
+    _assert_parity(stats, max_band_frac=0.01)
+    assert stats["hits"] > 500
+    # rays with no candidates are misses
+    assert np.all(seg[counts == 0] == -1)
