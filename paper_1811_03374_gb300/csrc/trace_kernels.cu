@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_persistent(const TraceArgs a) {
 
   // lane state
   int64_t ray = -1;
-  int32_t cand = 0, cend = 0, pc = 0, pend = 0, cur_seg = -1, cur_piece = -1;
+  int32_t cand = 0, crow = 0, cend = 0, pc = 0, pend = 0, cur_seg = -1, cur_piece = -1;
   RayFrame rf;
   float ray_tmax = 0.0f;
   float best_t = 0.0f, best_u = -1.0f;
@@ -89,55 +89,56 @@ __global__ void __launch_bounds__(256) k_persistent(const TraceArgs a) {
   PairState st;
   unsigned long long n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
 
+  // Moves the lane to its next piece; finishes candidates (pairs mode) and
+  // the ray when they run out.  Returns true when a piece is ready.
+  auto next_piece = [&]() -> bool {
+    while (ray >= 0) {
+      if (pc < pend) {
+        cur_piece = pc++;
+        return true;
+      }
+      if (PAIRS && cand >= crow) {
+        a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
+        if (a.leaf) a.leaf[cand] = cand_leaf;
+      }
+      if (++cand < cend) {
+        const int32_t s = __ldg(a.seg_idx + cand);
+        if (PAIRS) {
+          cand_t = ray_tmax;
+          cand_u = -1.0f;
+          cand_leaf = -1;
+        }
+        if (CHECK && (s < 0 || s >= a.n_seg)) {
+          atomicOr(a.status, FX_DEV_BAD_INDEX);
+          pc = pend = 0;
+          cand_t = kInf;
+          continue;
+        }
+        cur_seg = s;
+        if (a.identity) {
+          pc = s;
+          pend = s + 1;
+        } else {
+          pc = __ldg(a.piece_begin + s);
+          pend = __ldg(a.piece_begin + s + 1);
+        }
+      } else {
+        if (!PAIRS) {
+          const bool hit = best_seg >= 0;
+          a.tu[ray] = make_float2(hit ? best_t : kInf, hit ? best_u : -1.0f);
+          a.seg[ray] = best_seg;
+          if (a.leaf) a.leaf[ray] = best_leaf;
+        }
+        ray = -1;
+      }
+    }
+    return false;
+  };
+
   for (;;) {
     // ---- 1. acquire a (ray, piece) pair for every idle lane ---------------
     bool fresh = false;
-    if (!active && !done) {
-      // advance within the current ray
-      while (ray >= 0) {
-        if (pc < pend) {
-          cur_piece = pc++;
-          fresh = true;
-          break;
-        }
-        if (PAIRS && cand < cend) {
-          a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
-          if (a.leaf) a.leaf[cand] = cand_leaf;
-        }
-        if (++cand < cend) {
-          int32_t s = __ldg(a.seg_idx + cand);
-          if (CHECK && (s < 0 || s >= a.n_seg)) {
-            atomicOr(a.status, FX_DEV_BAD_INDEX);
-            pc = pend = 0;
-            cand_t = kInf;
-            cand_u = -1.0f;
-            cand_leaf = -1;
-            continue;
-          }
-          cur_seg = s;
-          if (a.identity) {
-            pc = s;
-            pend = s + 1;
-          } else {
-            pc = __ldg(a.piece_begin + s);
-            pend = __ldg(a.piece_begin + s + 1);
-          }
-          if (PAIRS) {
-            cand_t = ray_tmax;
-            cand_u = -1.0f;
-            cand_leaf = -1;
-          }
-        } else {
-          if (!PAIRS) {
-            const bool hit = best_seg >= 0;
-            a.tu[ray] = make_float2(hit ? best_t : kInf, hit ? best_u : -1.0f);
-            a.seg[ray] = best_seg;
-            if (a.leaf) a.leaf[ray] = best_leaf;
-          }
-          ray = -1;
-        }
-      }
-    }
+    if (!active && !done) fresh = next_piece();
     // lanes without a ray take new rays from the warp pool
     for (;;) {
       const bool want = !active && !done && !fresh && ray < 0;
@@ -161,57 +162,26 @@ __global__ void __launch_bounds__(256) k_persistent(const TraceArgs a) {
       const int rank = __popc(m & lt_mask);
       const int64_t avail = pool_end - pool_next;
       if (want && rank < avail) {
-        ray = pool_next + rank;
-        rf = load_ray<FAST>(a.rays, ray, ray_tmax);
-        best_t = ray_tmax;
-        best_u = -1.0f;
-        best_seg = -1;
-        best_leaf = -1;
-        cand = __ldg(a.row_ptr + ray) - 1;
-        cend = __ldg(a.row_ptr + ray + 1);
-        pc = pend = 0;
-        // walk to the first piece (or finish an empty row)
-        while (ray >= 0) {
-          if (pc < pend) {
-            cur_piece = pc++;
-            fresh = true;
-            break;
+        const int64_t r = pool_next + rank;
+        crow = __ldg(a.row_ptr + r);
+        cend = __ldg(a.row_ptr + r + 1);
+        if (crow >= cend) {
+          // no candidates: a miss, without loading the ray
+          if (!PAIRS) {
+            a.tu[r] = make_float2(kInf, -1.0f);
+            a.seg[r] = -1;
+            if (a.leaf) a.leaf[r] = -1;
           }
-          if (PAIRS && cand >= 0 && cand < cend && cand >= __ldg(a.row_ptr + ray)) {
-            a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
-            if (a.leaf) a.leaf[cand] = cand_leaf;
-          }
-          if (++cand < cend) {
-            int32_t s = __ldg(a.seg_idx + cand);
-            if (CHECK && (s < 0 || s >= a.n_seg)) {
-              atomicOr(a.status, FX_DEV_BAD_INDEX);
-              pc = pend = 0;
-              cand_t = kInf;
-              cand_u = -1.0f;
-              cand_leaf = -1;
-              continue;
-            }
-            cur_seg = s;
-            if (a.identity) {
-              pc = s;
-              pend = s + 1;
-            } else {
-              pc = __ldg(a.piece_begin + s);
-              pend = __ldg(a.piece_begin + s + 1);
-            }
-            if (PAIRS) {
-              cand_t = ray_tmax;
-              cand_u = -1.0f;
-              cand_leaf = -1;
-            }
-          } else {
-            if (!PAIRS) {
-              a.tu[ray] = make_float2(kInf, -1.0f);
-              a.seg[ray] = -1;
-              if (a.leaf) a.leaf[ray] = -1;
-            }
-            ray = -1;
-          }
+        } else {
+          ray = r;
+          rf = load_ray<FAST>(a.rays, ray, ray_tmax);
+          best_t = ray_tmax;
+          best_u = -1.0f;
+          best_seg = -1;
+          best_leaf = -1;
+          cand = crow - 1;
+          pc = pend = 0;
+          fresh = next_piece();
         }
       }
       pool_next += min((int64_t)__popc(m), avail);

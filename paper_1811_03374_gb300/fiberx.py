@@ -284,6 +284,7 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, cps, rays, row_ptr, seg_idx, depth, fibers, flags=0):
+            rays, row_ptr, seg_idx = _inputs(fibers, rays, row_ptr, seg_idx)
             tu, seg, _ = intersect_closest(fibers, rays, row_ptr, seg_idx, depth, flags=flags, leaf=False)
             ctx.fibers = fibers
             ctx.save_for_backward(rays, tu, seg)

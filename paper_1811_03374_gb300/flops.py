@@ -1,0 +1,43 @@
+"""Algorithmic FP32 work of the traversal, per counted event.
+
+Counts follow the arithmetic of each step as the kernels perform it (an add,
+subtract or multiply is one flop, a fused multiply-add two, a reciprocal,
+division or square root one); comparisons, selects and integer bit-string
+work are not counted.
+
+  per ray      normalise the direction, Duff et al.'s basis          20
+  per test     origin offset + rotation of (p, d, t0, t1), slab      78
+  per node     conservative radius (44) + unit-ray cylinder (24)     68
+  per descent  split terms, plane, child selection                   49
+  per backtrack  power-form recomputation (142) + slab (15)         157
+  per hit      u by projection onto the leaf axis, segment mapping   17
+"""
+
+PER_RAY = 20
+PER_TEST = 78
+PER_NODE = 68
+PER_DESCENT = 49
+PER_BACKTRACK = 157
+PER_HIT = 17
+
+# Bytes a closest-hit launch must move at least once: ray (32 B) and two
+# row_ptr words per ray, one seg_idx word per pair, 64 B per piece touched,
+# 16 B of output per ray (tu, seg, leaf).
+BYTES_PER_RAY = 32 + 8 + 16
+BYTES_PER_PAIR = 4
+BYTES_PER_PIECE = 64
+
+
+def alg_flops(counters, n_ray_with_candidates):
+    c = counters
+    return (PER_RAY * n_ray_with_candidates + PER_TEST * c["tests"] + PER_NODE * c["nodes"]
+            + PER_DESCENT * c["descents"] + PER_BACKTRACK * c["backtracks"] + PER_HIT * c["hits"])
+
+
+def alg_bytes(n_ray, n_pair, n_piece_touched):
+    return BYTES_PER_RAY * n_ray + BYTES_PER_PAIR * n_pair + BYTES_PER_PIECE * n_piece_touched
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    """FP32 FMA peak: 128 lanes per SM, 2 flops per FMA."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
