@@ -171,8 +171,15 @@ def oracle_rate(case, depth, seconds, seed=7):
         if dt >= 0.5 * seconds or frac >= 1.0:
             break
         frac = min(1.0, frac * max(2.0, 0.8 * seconds / max(dt, 1e-3)))
-    return dict(value=pairs / dt / 1e9, pairs=pairs, rays=len(idx), seconds=dt, frac=len(idx) / n,
-                cores=O.num_threads())
+    reps = 1
+    while dt * reps < 0.5 * seconds:  # the whole frame is cheap: repeat it
+        t0 = time.perf_counter()
+        O.closest(sub, depth, pieces)
+        dt_r = time.perf_counter() - t0
+        dt = (dt * reps + dt_r) / (reps + 1)
+        reps += 1
+    return dict(value=pairs / dt / 1e9, pairs=pairs, rays=len(idx), seconds=dt * reps, frac=len(idx) / n,
+                cores=O.num_threads(), reps=reps)
 
 
 def run_reference(args):
@@ -359,8 +366,8 @@ def main():
         r = oracle_rate(case, depth, args.cpu_seconds)
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": "%d seeded rays (%.2f%% of the frame) with their %d candidate pairs, "
-                         "FP64 oracle, OpenMP over rays, %.1f s" % (r["rays"], 100 * r["frac"], r["pairs"],
-                                                                    r["seconds"])}
+                         "FP64 oracle, OpenMP over rays, %d repetition(s), %.1f s" % (
+                             r["rays"], 100 * r["frac"], r["pairs"], r["reps"], r["seconds"])}
 
     emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

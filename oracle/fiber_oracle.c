@@ -512,14 +512,50 @@ void orc_intersect(const double *ray7, const double *cp, int depth, orc_hit *h)
 static int piece_depth(int depth, int level) { return depth > level ? depth - level : 0; }
 
 /*
- * Closest hit per ray over its CSR candidates (Sec. 3.2, immediate
- * termination; Sec. 4 "closer segments are always intersected first" applied
- * across candidates): candidates in row order, pieces of a segment in order;
- * the best t so far is the t_max of the next test (reading R7) and only a
- * strictly closer hit replaces it, so ties keep the earlier candidate.
- * Outputs t (inf on miss), u in the segment's parameter (-1), segment (-1),
- * leaf start in units of 2^-23 of the segment (-1).  counters (nullable):
- * [nodes, descents, backtracks, hits, tests].
+ * One candidate segment against a ray: its pieces in order, each traversed to
+ * depth - level (reading R15); the pieces' best hit (ties keep the earlier
+ * piece, so a piece is tested with the best t of the earlier pieces as t_max).
+ * Returns 1 on a hit closer than tmax; u and leaf refer to the segment.
+ */
+static int candidate_hit(const ray_t *r, int32_t s, const double *piece_cp,
+                         const int32_t *piece_begin, const int32_t *piece_level,
+                         const int32_t *piece_off, int depth, double tmax, double *t_out,
+                         double *u_out, int32_t *leaf_out, int64_t *cn, int64_t *cd, int64_t *cb,
+                         int64_t *ch, int64_t *ct)
+{
+    double best = tmax, bu = -1.0;
+    int32_t bl = -1;
+    int got = 0;
+    for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
+        v4 Q[4];
+        orc_hit h;
+        to_ray_frame(r, piece_cp + 16 * k, Q);
+        int lv = piece_level[k];
+        traverse(Q, piece_depth(depth, lv), best, &h);
+        *cn += h.nodes; *cd += h.descents; *cb += h.backtracks; *ct += 1;
+        if (h.hit && h.t < best) {
+            *ch += 1;
+            best = h.t;
+            bu = (piece_off[k] + h.u) * ldexp(1.0, -lv);
+            bl = (int32_t)(((int64_t)piece_off[k] << (23 - lv)) + (h.leaf >> lv));
+            got = 1;
+        }
+    }
+    *t_out = got ? best : INFINITY;
+    *u_out = bu;
+    *leaf_out = bl;
+    return got;
+}
+
+/*
+ * Closest hit per ray over its CSR candidates: the smallest t among the
+ * candidates' own hits, each candidate tested with the ray's t_max; ties keep
+ * the earlier candidate (row order).  The top-level structure that supplies
+ * candidates is orthogonal to the intersector (Sec. 2, Sec. 4), so the ray's
+ * result is the plain minimum over independent candidate tests.  Outputs t
+ * (inf on miss), u in the segment's parameter (-1), segment (-1), leaf start
+ * in units of 2^-23 of the segment (-1).  counters (nullable): [nodes,
+ * descents, backtracks, accepted leaf hits, piece tests].
  */
 void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
                  const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
@@ -535,28 +571,20 @@ void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : cn, cd, cb, ch, ct)
     for (int64_t i = 0; i < n_ray; ++i) {
         ray_t r = make_ray_f(rays + 8 * i);
-        double best = r.tmax, bu = -1.0;
+        double best = INFINITY, bu = -1.0;
         int32_t bs = -1, bl = -1;
         for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
-            int32_t s = seg_idx[j];
-            for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
-                v4 Q[4];
-                orc_hit h;
-                to_ray_frame(&r, piece_cp + 16 * k, Q);
-                int lv = piece_level[k];
-                traverse(Q, piece_depth(depth, lv), best, &h);
-                cn += h.nodes; cd += h.descents; cb += h.backtracks; ct += 1;
-                if (h.hit && h.t < best) {
-                    double scale = ldexp(1.0, -lv);
-                    best = h.t;
-                    bu = (piece_off[k] + h.u) * scale;
-                    bs = s;
-                    bl = (int32_t)(((int64_t)piece_off[k] << (23 - lv)) + (h.leaf >> lv));
-                }
+            double t, u;
+            int32_t leaf;
+            if (candidate_hit(&r, seg_idx[j], piece_cp, piece_begin, piece_level, piece_off, depth,
+                              r.tmax, &t, &u, &leaf, &cn, &cd, &cb, &ch, &ct) && t < best) {
+                best = t;
+                bu = u;
+                bs = seg_idx[j];
+                bl = leaf;
             }
         }
-        if (bs >= 0) ch += 1;
-        t_out[i] = bs >= 0 ? best : INFINITY;
+        t_out[i] = best;
         u_out[i] = bu;
         seg_out[i] = bs;
         if (leaf_out) leaf_out[i] = bl;
@@ -566,8 +594,8 @@ void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const
     }
 }
 
-/* Per-pair hits: each candidate tested with the ray's own t_max; pieces of a
- * segment combined by the closest rule above.  Outputs indexed by pair. */
+/* Per-pair hits: each candidate tested with the ray's own t_max (see
+ * candidate_hit).  Outputs indexed by pair. */
 void orc_pairs(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
                const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
                const int32_t *piece_off, int depth, int nthreads, double *t_out, double *u_out,
@@ -583,27 +611,10 @@ void orc_pairs(const float *rays, int64_t n_ray, const int32_t *row_ptr, const i
     for (int64_t i = 0; i < n_ray; ++i) {
         ray_t r = make_ray_f(rays + 8 * i);
         for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
-            int32_t s = seg_idx[j];
-            double best = r.tmax, bu = -1.0;
-            int32_t bl = -1, got = 0;
-            for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
-                v4 Q[4];
-                orc_hit h;
-                to_ray_frame(&r, piece_cp + 16 * k, Q);
-                int lv = piece_level[k];
-                traverse(Q, piece_depth(depth, lv), best, &h);
-                cn += h.nodes; cd += h.descents; cb += h.backtracks; ct += 1;
-                if (h.hit && h.t < best) {
-                    best = h.t;
-                    bu = (piece_off[k] + h.u) * ldexp(1.0, -lv);
-                    bl = (int32_t)(((int64_t)piece_off[k] << (23 - lv)) + (h.leaf >> lv));
-                    got = 1;
-                }
-            }
-            ch += got;
-            t_out[j] = got ? best : INFINITY;
-            u_out[j] = bu;
-            if (leaf_out) leaf_out[j] = bl;
+            int32_t leaf;
+            candidate_hit(&r, seg_idx[j], piece_cp, piece_begin, piece_level, piece_off, depth, r.tmax,
+                          &t_out[j], &u_out[j], &leaf, &cn, &cd, &cb, &ch, &ct);
+            if (leaf_out) leaf_out[j] = leaf;
         }
     }
     if (counters) {

@@ -94,7 +94,13 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
     return FX_OK;
   }
   FX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s));
-  FX_CUDA(fx::launch_persistent(a, pairs, flags, grid_for(f, pairs, flags), f->launch.block, s));
+  int variant = f->launch.variant;
+  if (variant == FX_VARIANT_AUTO) variant = a.n_pair >= 8 * a.n_ray ? FX_VARIANT_WARP : FX_VARIANT_LANE;
+  if (variant == FX_VARIANT_WARP) {
+    FX_CUDA(fx::launch_warp_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
+  } else {
+    FX_CUDA(fx::launch_persistent(a, pairs, flags, grid_for(f, pairs, flags), f->launch.block, s));
+  }
   return FX_OK;
 }
 
@@ -224,6 +230,7 @@ fx_status fx_set_launch(fx_fibers* f, const fx_launch* cfg) {
   if (!(b == 64 || b == 128 || b == 256)) return fail(FX_EINVAL, "block must be 64, 128 or 256");
   if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 16) return fail(FX_EINVAL, "blocks_per_sm outside [0, 16]");
   if (cfg->chunk < 1 || cfg->chunk > 1024) return fail(FX_EINVAL, "chunk outside [1, 1024]");
+  if (cfg->variant < FX_VARIANT_AUTO || cfg->variant > FX_VARIANT_WARP) return fail(FX_EINVAL, "unknown variant");
   f->launch = *cfg;
   return FX_OK;
 }

@@ -273,4 +273,93 @@ __device__ __forceinline__ float leaf_u(const Node& c, float t, uint32_t start, 
   return fmaf(ul, __uint2float_rn(size), __uint2float_rn(start)) * kUnit;
 }
 
+// ---------------------------------------------------------------------------
+// per-(ray, piece) traversal state shared by the kernels
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int iter_cap(int depth) { return 1024 + 64 * depth; }
+
+__device__ __forceinline__ int piece_min_size_shift(int depth, int level) {
+  const int d = depth > level ? depth - level : 0;
+  return 23 - d;
+}
+
+// State of one lane's current (ray, piece) test.
+struct PairState {
+  Node R;  // root node of the piece in the ray frame (for backtracking)
+  Node c;  // current node
+  float tmin, tmax;
+  uint32_t bits, start, size, min_size;
+  int32_t info;  // level | off << 4 | unsupported << 31
+  int32_t iters;
+};
+
+// Starts a test of piece data (p, d, t0, t1), world space, against the ray.
+template <bool FAST>
+__device__ __forceinline__ void begin_local(PairState& st, const float4& p, const float4& d,
+                                            const float4& t0, const float4& t1, const RayFrame& r,
+                                            int32_t info, int depth, float pair_tmax) {
+  st.R.p = rotate(r, p.x - r.o.x, p.y - r.o.y, p.z - r.o.z, p.w);
+  st.R.d = rotate(r, d.x, d.y, d.z, d.w);
+  st.R.t0 = rotate(r, t0.x, t0.y, t0.z, t0.w);
+  st.R.t1 = rotate(r, t1.x, t1.y, t1.z, t1.w);
+  st.c = st.R;
+  st.bits = 0;
+  st.start = 0;
+  st.size = kRootSize;
+  st.info = info;
+  st.min_size = 1u << piece_min_size_shift(depth, info & 15);
+  st.iters = 0;
+  slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
+}
+
+template <bool FAST>
+__device__ __forceinline__ void begin_piece(PairState& st, const float4* __restrict__ piece, int k,
+                                            const RayFrame& r, int32_t info, int depth,
+                                            float pair_tmax) {
+  begin_local<FAST>(st, __ldg(piece + 4 * k), __ldg(piece + 4 * k + 1), __ldg(piece + 4 * k + 2),
+                    __ldg(piece + 4 * k + 3), r, info, depth, pair_tmax);
+}
+
+// Segment-parameter u and leaf start of a piece-local hit.
+__device__ __forceinline__ void to_segment(int32_t info, float u_piece, uint32_t start, float& u,
+                                           int32_t& leaf) {
+  const int lvl = info & 15;
+  const int off = (info >> 4) & 0x7ffff;
+  u = lvl ? ldexpf(__int2float_rn(off) + u_piece, -lvl) : u_piece;
+  leaf = (int32_t)(((uint32_t)off << (23 - lvl)) + (start >> lvl));
+}
+
+// Outcome of one node step.
+enum StepResult { kStepContinue = 0, kStepLeaf = 1, kStepDone = 2 };
+
+// One node test (Sec. 3.2 / 3.3) and the move it implies: leaf, descent or
+// backtrack.  On kStepLeaf, t is the entry into the capped leaf cylinder,
+// max(c0, t_min), and the test of this piece ends (instant termination); on
+// kStepDone the piece is exhausted without a hit.
+template <bool FAST, bool COUNT>
+__device__ __forceinline__ StepResult node_step(PairState& st, float pair_tmax, float& t,
+                                                unsigned long long& nd, unsigned long long& nb) {
+  const float r = cons_radius<FAST>(st.c);
+  float c0 = 0.0f, c1 = 0.0f;
+  const bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1) &&
+                    fmaxf(c0, st.tmin) <= fminf(c1, st.tmax);
+  ++st.iters;
+  if (over && st.size <= st.min_size) {
+    t = fmaxf(c0, st.tmin);
+    return kStepLeaf;
+  }
+  if (over) {
+    descend<FAST>(st.c, c0, c1, st.tmin, st.tmax, st.bits, st.start, st.size);
+    if (COUNT) ++nd;
+    return kStepContinue;
+  }
+  if (st.bits == 0u) return kStepDone;
+  jump_up(st.bits, st.start, st.size);
+  recompute(st.R, st.start, st.size, st.c);
+  slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
+  if (COUNT) ++nb;
+  return kStepContinue;
+}
+
 }  // namespace fx

@@ -23,46 +23,6 @@ namespace fx {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int iter_cap(int depth) { return 1024 + 64 * depth; }
-
-__device__ __forceinline__ int piece_min_size_shift(int depth, int level) {
-  const int d = depth > level ? depth - level : 0;
-  return 23 - d;
-}
-
-// State of one lane's current (ray, piece) test.
-struct PairState {
-  Node R;      // root node of the piece in the ray frame (for backtracking)
-  Node c;      // current node
-  float tmin, tmax;
-  uint32_t bits, start, size, min_size;
-  int32_t info;  // level | off << 4 | unsupported << 31
-  int32_t iters;
-};
-
-template <bool FAST>
-__device__ __forceinline__ void begin_pair(PairState& st, const TraceArgs& a, int piece,
-                                           const RayFrame& rf, float pair_tmax) {
-  st.R = load_local(a.piece, piece, rf);
-  st.c = st.R;
-  st.bits = 0;
-  st.start = 0;
-  st.size = kRootSize;
-  st.info = a.identity ? 0 : __ldg(a.piece_info + piece);
-  st.min_size = 1u << piece_min_size_shift(a.depth, st.info & 15);
-  st.iters = 0;
-  slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
-}
-
-// Segment-parameter u and leaf start of a piece-local hit.
-__device__ __forceinline__ void to_segment(int32_t info, float u_piece, uint32_t start, float& u,
-                                           int32_t& leaf) {
-  const int lvl = info & 15;
-  const int off = (info >> 4) & 0x7ffff;
-  u = lvl ? ldexpf(__int2float_rn(off) + u_piece, -lvl) : u_piece;
-  leaf = (int32_t)(((uint32_t)off << (23 - lvl)) + (start >> lvl));
-}
-
 // ---------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------
@@ -189,7 +149,8 @@ __global__ void __launch_bounds__(256) k_persistent(const TraceArgs a) {
 
     // ---- 2. set up fresh pairs -------------------------------------------
     if (fresh) {
-      begin_pair<FAST>(st, a, cur_piece, rf, PAIRS ? cand_t : best_t);
+      begin_piece<FAST>(st, a.piece, cur_piece, rf, a.identity ? 0 : __ldg(a.piece_info + cur_piece), a.depth,
+                        PAIRS ? cand_t : best_t);
       active = true;
       if (COUNT) ++n_tests;
     }
@@ -272,7 +233,7 @@ __device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const
                                             float pair_tmax, float& t_out, float& u_out,
                                             int32_t& leaf_out, unsigned long long* cnt) {
   PairState st;
-  begin_pair<FAST>(st, a, piece, rf, pair_tmax);
+  begin_piece<FAST>(st, a.piece, piece, rf, a.identity ? 0 : __ldg(a.piece_info + piece), a.depth, pair_tmax);
   for (;;) {
     const float r = cons_radius<FAST>(st.c);
     float c0 = 0.0f, c1 = 0.0f;

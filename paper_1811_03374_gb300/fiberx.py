@@ -30,6 +30,10 @@ FX_POLISH_FP64 = 0x4
 FX_COUNT = 0x8
 FX_CHECK_INDEX = 0x10
 
+FX_VARIANT_AUTO = 0
+FX_VARIANT_LANE = 1
+FX_VARIANT_WARP = 2
+
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
            "intersect_backward", "intersect_closest_host", "fx_set_launch", "fx_get_launch",
@@ -53,7 +57,8 @@ class FibersInfo(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -163,10 +168,10 @@ class Fibers:
     def get_launch(self):
         c = Launch()
         _check(self._lib.fx_get_launch(self.handle, ctypes.byref(c)))
-        return dict(block=c.block, blocks_per_sm=c.blocks_per_sm, chunk=c.chunk)
+        return dict(block=c.block, blocks_per_sm=c.blocks_per_sm, chunk=c.chunk, variant=c.variant)
 
-    def set_launch(self, block=256, blocks_per_sm=0, chunk=32):
-        _check(self._lib.fx_set_launch(self.handle, ctypes.byref(Launch(block, blocks_per_sm, chunk))))
+    def set_launch(self, block=128, blocks_per_sm=0, chunk=32, variant=0):
+        _check(self._lib.fx_set_launch(self.handle, ctypes.byref(Launch(block, blocks_per_sm, chunk, variant))))
 
     def counters(self, reset=True, stream=None):
         out = np.zeros(5, dtype=np.uint64)
