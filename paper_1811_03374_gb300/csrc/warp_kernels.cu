@@ -236,7 +236,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             best_leaf = wl;
             best_seg = ws;
           }
-          if (active) st.tmax = fminf(st.tmax, best_t);
         }
       }
       if (!PAIRS && lane == 0) {

@@ -13,7 +13,8 @@ Layouts (all float32 unless noted):
 * ``rays``    -- ``[n_ray, 8]``: ``(o.x, o.y, o.z, t_max, w.x, w.y, w.z, 0)``;
   ``w`` is normalised in float64 before rounding.
 * ``row_ptr`` -- int32 ``[n_ray + 1]``, ``seg_idx`` -- int32 ``[n_pair]``:
-  candidate segments of each ray in CSR form, sorted by segment id per row.
+  candidate segments of each ray in CSR form (grid-cull rows list segments
+  front to back in the order the ray's walk meets them).
 
 Every generator takes an explicit seed; ``SEED_BASE + k`` is the default seed
 of workload ``k`` (0 tiny, 1 hair patch, 2 depth sweep, 3 precision stress,

@@ -7,8 +7,9 @@
  * segment's control-hull AABB, dilated by its largest control radius, is
  * binned into a uniform grid; each ray walks the grid with a 3-D DDA
  * (Amanatides & Woo) and collects the de-duplicated ids of every segment
- * registered in the cells it crosses.  The result is a CSR list per ray,
- * sorted by segment id.
+ * registered in the cells it crosses, in the order the walk first meets them
+ * (front to back along the ray; by id within a cell).  The result is a CSR
+ * list per ray.
  *
  * Host C only; the same source builds on x86-64 and aarch64.  Output does not
  * depend on the thread count.
@@ -97,12 +98,6 @@ static int grid_build(grid_t *g, const float *cps, int64_t n_seg, int nx, int ny
     return 0;
 }
 
-static int cmp_i32(const void *a, const void *b)
-{
-    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
-    return (x > y) - (x < y);
-}
-
 /* Walks one ray through the grid; appends unseen segment ids to buf. */
 static int64_t walk_ray(const grid_t *g, const float *ray, int32_t stamp_id, int32_t *stamp,
                         int32_t **buf, int64_t *cap)
@@ -161,7 +156,6 @@ static int64_t walk_ray(const grid_t *g, const float *ray, int32_t stamp_id, int
         if (c[a] < 0 || c[a] >= g->n[a]) break;
         tnext[a] += tdelta[a];
     }
-    qsort(*buf, (size_t)n, sizeof(int32_t), cmp_i32);
     return n;
 }
 

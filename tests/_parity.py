@@ -16,14 +16,18 @@ shifted sideways (8 directions orthogonal to it) by the resolution band
 1e-4 r is the silhouette band within which hit/miss may differ, the second
 term is the spacing of FP32 coordinates along the ray, below which no FP32
 computation can resolve a decision (a silhouette, a split plane, an end
-plane).  A ray passes "in band" if the oracle result for one shifted copy
-meets the strict rule; every other ray is a failure.
+plane) or place a hit (for a ray nearly parallel to a fiber a sideways
+error e moves the hit along the fiber by e / tan(angle)).  A ray passes "in
+band" if its hit status and segment occur among the oracle results of the
+nominal and shifted rays and its t and u lie within the range those results
+span, widened by the strict tolerances; every other ray is a failure.
 """
 import numpy as np
 
 import oracle as O
 
 TOL_T = 1e-5
+P_TOL_T = TOL_T
 TOL_U = 1e-5
 EPS32 = 2.0 ** -24
 
@@ -102,11 +106,27 @@ def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
                seg_idx=np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32))
     ref = O.closest(sub, depth, pieces)
     m = len(idx)
-    ok = np.zeros(m, dtype=bool)
     tol_u = u_tolerance(case, case["rays"][idx], s_g[idx], t_g[idx], u_g[idx])
-    for k in range(len(dirs)):
-        sl = slice(k * m, (k + 1) * m)
-        ok |= strict_ok(t_g[idx], u_g[idx], s_g[idx], ref["t"][sl], ref["u"][sl], ref["seg"][sl], tol_u)
+    nominal = O.closest(dict(cps=case["cps"], rays=case["rays"][idx],
+                             row_ptr=np.array(rows[:m + 1], dtype=np.int32) if m else np.zeros(1, np.int32),
+                             seg_idx=np.concatenate(segs[:m]).astype(np.int32) if m else np.zeros(0, np.int32)),
+                        depth, pieces)
+    T = np.stack([nominal["t"]] + [ref["t"][k * m:(k + 1) * m] for k in range(len(dirs))])
+    U = np.stack([nominal["u"]] + [ref["u"][k * m:(k + 1) * m] for k in range(len(dirs))])
+    S = np.stack([nominal["seg"]] + [ref["seg"][k * m:(k + 1) * m] for k in range(len(dirs))])
+    tg, ug, sg = t_g[idx], u_g[idx], s_g[idx]
+    ok = np.zeros(m, dtype=bool)
+    for i in range(m):
+        same = S[:, i] == sg[i]
+        if not same.any():
+            continue
+        if sg[i] < 0:
+            ok[i] = True
+            continue
+        tt, uu = T[same, i], U[same, i]
+        tol_t = P_TOL_T * np.abs(tt).max()
+        ok[i] = (tt.min() - tol_t <= tg[i] <= tt.max() + tol_t and
+                 uu.min() - tol_u[i] <= ug[i] <= uu.max() + tol_u[i])
     return idx[ok]
 
 

@@ -31,7 +31,7 @@ def test_hair_fibers_shape_chain_and_taper():
     assert np.all(cps[:, 0, 0, 2] == 0) and cps[:, 0, 0, :2].min() >= 0 and cps[:, 0, 0, :2].max() <= 1
 
 
-def test_grid_cull_is_conservative_and_sorted():
+def test_grid_cull_is_conservative_and_deduplicated():
     # every segment whose dilated AABB a ray crosses must be listed
     cps = I.hair_fibers(n_fibers=300)
     rays, _ = I.pinhole_rays(width=64, height=36)
@@ -42,7 +42,7 @@ def test_grid_cull_is_conservative_and_sorted():
     lo, hi = c[:, :, :3].min(1) - rmax, c[:, :, :3].max(1) + rmax
     for i in range(0, len(rays), 7):
         row = si[rp[i]:rp[i + 1]]
-        assert np.all(np.diff(row) > 0)
+        assert len(np.unique(row)) == len(row)
         o, w = rays[i, :3].astype(np.float64), rays[i, 4:7].astype(np.float64)
         with np.errstate(divide="ignore", invalid="ignore"):
             ta, tb = (lo - o) / w, (hi - o) / w
