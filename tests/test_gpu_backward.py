@@ -1,0 +1,126 @@
+"""The hand-written adjoint kernel (intersect_backward, through the C ABI and
+the autograd Function) against the oracle's implicit-function gradient of the
+limit-surface hit, on hair-patch geometry.  The oracle computes its own
+forward hits; nothing from the CUDA path enters it."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_03374_gb300 import fiberx as F
+from paper_1811_03374_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+DEPTH = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _oracle_grad(case, weights, depth):
+    """sum_i w_i dt_i/dtheta per segment, from the oracle's own hits."""
+    ref = O.closest(case, depth)
+    g = np.zeros((case["cps"].shape[0], 4, 4))
+    used = np.zeros(len(weights), dtype=bool)
+    for i in np.nonzero(ref["seg"] >= 0)[0]:
+        s = ref["seg"][i]
+        u = ref["u"][i]
+        if u <= 0.0 or u >= 1.0:
+            continue  # end-disk hits are checked separately
+        r7 = O.ray7_from_packed(case["rays"][i])
+        gi = O.grad_t(r7, case["cps"][s].astype(np.float64), ref["t"][i], u)
+        if gi is None:
+            continue
+        g[s] += weights[i] * gi
+        used[i] = True
+    return g, used, ref
+
+
+@pytest.fixture(scope="module")
+def hair_hits():
+    case = I.aimed_hair_case(4096)
+    w = I.hit_weights(4096)
+    g_ref, used, ref = _oracle_grad(case, w, DEPTH)
+    return case, w, g_ref, used, ref
+
+
+def test_backward_matches_oracle_ift(hair_hits):
+    case, w, g_ref, used, ref = hair_hits
+    fib = F.Fibers(case["cps"])
+    tu, seg, _ = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], DEPTH)
+    # the oracle's selection of usable hits (lateral, non-singular) decides
+    # which rays carry weight, so both sides sum the same terms
+    wt = torch.tensor(np.where(used, w, 0.0).astype(np.float32), device="cuda")
+    g, skipped = F.intersect_backward(fib, case["rays"], tu, seg, wt)
+    g = g.cpu().numpy().astype(np.float64)
+    fib.close()
+    assert used.sum() > 3500
+    err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert err < 1e-3, err
+    # per segment, with an absolute floor of 1e-6 of the largest entry
+    floor = 1e-6 * np.abs(g_ref).max()
+    per = np.linalg.norm((g - g_ref).reshape(len(g), -1), axis=1) / (
+        np.linalg.norm(g_ref.reshape(len(g), -1), axis=1) + floor)
+    assert np.quantile(per[np.abs(g_ref).reshape(len(g), -1).max(1) > 0], 0.999) < 1e-2
+    assert per.max() < 5e-2
+
+
+def test_autograd_function_matches_adjoint(hair_hits):
+    case, w, g_ref, used, ref = hair_hits
+    fib = F.Fibers(case["cps"])
+    cps = torch.tensor(case["cps"], device="cuda", requires_grad=True)
+    t, u, s = F.fiber_intersect(cps, case["rays"], case["row_ptr"], case["seg_idx"], DEPTH, fib)
+    wt = torch.tensor(np.where(used, w, 0.0).astype(np.float32), device="cuda")
+    loss = (torch.where(s >= 0, t, torch.zeros_like(t)) * wt).sum()
+    loss.backward()
+    g = cps.grad.cpu().numpy().astype(np.float64)
+    fib.close()
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) < 1e-3
+
+
+def test_backward_accumulates_and_skips_misses():
+    case = I.aimed_hair_case(512, seed=99)
+    fib = F.Fibers(case["cps"])
+    tu, seg, _ = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], DEPTH)
+    ones = torch.ones(512, device="cuda")
+    g1, _ = F.intersect_backward(fib, case["rays"], tu, seg, ones)
+    g2 = g1.clone()
+    F.intersect_backward(fib, case["rays"], tu, seg, ones, grad_cps=g2)
+    np.testing.assert_allclose(g2.cpu().numpy(), 2 * g1.cpu().numpy(), rtol=1e-6, atol=1e-9)
+    # a miss contributes nothing
+    seg_m = torch.full_like(seg, -1)
+    g3, sk = F.intersect_backward(fib, case["rays"], tu, seg_m, ones)
+    assert float(g3.abs().max()) == 0.0 and int(sk.item()) == 0
+    fib.close()
+
+
+def test_backward_translation_identity():
+    # moving every fiber along a ray by e moves that ray's hit by e: for a
+    # single ray, sum_k dt/dp_k . w = 1
+    case = I.aimed_hair_case(256, seed=7)
+    fib = F.Fibers(case["cps"])
+    tu, seg, _ = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], DEPTH)
+    seg_np, u_np = seg.cpu().numpy(), tu[:, 1].cpu().numpy()
+    checked = 0
+    for i in range(256):
+        if seg_np[i] < 0 or u_np[i] <= 0 or u_np[i] >= 1:
+            continue
+        gt = torch.zeros(256, device="cuda")
+        gt[i] = 1.0
+        g, sk = F.intersect_backward(fib, case["rays"], tu, seg, gt)
+        if int(sk.item()):
+            continue
+        gs = g[seg_np[i]].cpu().numpy().astype(np.float64)
+        w = case["rays"][i, 4:7].astype(np.float64)
+        w /= np.linalg.norm(w)
+        assert abs(gs[:, :3].sum(axis=0) @ w - 1.0) < 2e-3
+        checked += 1
+        if checked >= 40:
+            break
+    fib.close()
+    assert checked >= 30
