@@ -170,8 +170,9 @@ fx_status intersect_pairs(const fx_fibers *f, const float *rays, int64_t n_ray,
  * Inputs: rays (as above), tu and seg from intersect_closest, grad_t (n_ray
  * floats, dL/dt_i).  Output: grad_cps (n_seg x 16 floats, same layout as
  * cps), ACCUMULATED (+=) with atomics; zero it first for a fresh gradient.
- * Misses and singular systems (|det J| tiny, grazing) contribute nothing;
- * their count is added to *n_skipped_dev (device int64, nullable).
+ * Misses and rays with grad_t == 0 contribute nothing; hits whose system
+ * is singular (|det J| tiny: grazing) are skipped and counted in
+ * *n_skipped_dev (device int64, nullable).
  */
 fx_status intersect_backward(const fx_fibers *f, const float *rays, int64_t n_ray,
                              const float *tu, const int32_t *seg, const float *grad_t,

@@ -73,6 +73,8 @@ def lib():
             L.orc_intersect.restype = None
             L.orc_closest.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp]
             L.orc_closest.restype = None
+            L.orc_closest_d.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp]
+            L.orc_closest_d.restype = None
             L.orc_pairs.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
             L.orc_pairs.restype = None
             L.orc_to_ray_frame.argtypes = [vp, vp, vp]; L.orc_to_ray_frame.restype = None
@@ -171,6 +173,19 @@ def closest(case, depth, pieces=None, nthreads=0):
                       _p(cnt))
     return dict(t=t, u=u, seg=seg, leaf=leaf,
                 counters=dict(zip(["nodes", "descents", "backtracks", "hits", "tests"], cnt.tolist())))
+
+
+def closest_d(rays7, row_ptr, seg_idx, depth, pieces, nthreads=0):
+    """closest() with double-precision rays [n, 7] (o, w, t_max)."""
+    rays7 = np.ascontiguousarray(rays7, dtype=np.float64)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    si = np.ascontiguousarray(seg_idx, dtype=np.int32)
+    pc = np.ascontiguousarray(pieces["cp"], dtype=np.float64).reshape(-1, 16)
+    n = rays7.shape[0]
+    t = np.zeros(n); u = np.zeros(n); seg = np.zeros(n, np.int32); leaf = np.zeros(n, np.int32)
+    lib().orc_closest_d(_p(rays7), n, _p(rp), _p(si), _p(pc), _p(pieces["begin"]), _p(pieces["level"]),
+                        _p(pieces["off"]), int(depth), int(nthreads), _p(t), _p(u), _p(seg), _p(leaf), None)
+    return dict(t=t, u=u, seg=seg, leaf=leaf)
 
 
 def pairs(case, depth, pieces=None, nthreads=0):

@@ -557,10 +557,11 @@ static int candidate_hit(const ray_t *r, int32_t s, const double *piece_cp,
  * in units of 2^-23 of the segment (-1).  counters (nullable): [nodes,
  * descents, backtracks, accepted leaf hits, piece tests].
  */
-void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
-                 const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
-                 const int32_t *piece_off, int depth, int nthreads, double *t_out, double *u_out,
-                 int32_t *seg_out, int32_t *leaf_out, int64_t *counters)
+static void closest_impl(const float *rays_f, const double *rays_d, int64_t n_ray,
+                         const int32_t *row_ptr, const int32_t *seg_idx, const double *piece_cp,
+                         const int32_t *piece_begin, const int32_t *piece_level,
+                         const int32_t *piece_off, int depth, int nthreads, double *t_out,
+                         double *u_out, int32_t *seg_out, int32_t *leaf_out, int64_t *counters)
 {
     int64_t cn = 0, cd = 0, cb = 0, ch = 0, ct = 0;
 #ifdef _OPENMP
@@ -570,7 +571,7 @@ void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const
 #endif
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : cn, cd, cb, ch, ct)
     for (int64_t i = 0; i < n_ray; ++i) {
-        ray_t r = make_ray_f(rays + 8 * i);
+        ray_t r = rays_f ? make_ray_f(rays_f + 8 * i) : make_ray_d(rays_d + 7 * i);
         double best = INFINITY, bu = -1.0;
         int32_t bs = -1, bl = -1;
         for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
@@ -592,6 +593,26 @@ void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const
     if (counters) {
         counters[0] = cn; counters[1] = cd; counters[2] = cb; counters[3] = ch; counters[4] = ct;
     }
+}
+
+void orc_closest(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+                 const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+                 const int32_t *piece_off, int depth, int nthreads, double *t_out, double *u_out,
+                 int32_t *seg_out, int32_t *leaf_out, int64_t *counters)
+{
+    closest_impl(rays, NULL, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, piece_off,
+                 depth, nthreads, t_out, u_out, seg_out, leaf_out, counters);
+}
+
+/* The same with rays given in double precision (7 doubles: o, w, t_max). */
+void orc_closest_d(const double *rays7, int64_t n_ray, const int32_t *row_ptr,
+                   const int32_t *seg_idx, const double *piece_cp, const int32_t *piece_begin,
+                   const int32_t *piece_level, const int32_t *piece_off, int depth, int nthreads,
+                   double *t_out, double *u_out, int32_t *seg_out, int32_t *leaf_out,
+                   int64_t *counters)
+{
+    closest_impl(NULL, rays7, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, piece_off,
+                 depth, nthreads, t_out, u_out, seg_out, leaf_out, counters);
 }
 
 /* Per-pair hits: each candidate tested with the ray's own t_max (see

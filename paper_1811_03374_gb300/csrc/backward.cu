@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256)
   const int32_t s = seg[r];
   if (s < 0) return;
   const float gw = grad_t[r];
+  if (gw == 0.0f) return;  // contributes nothing
   const float4 ra = __ldg(rays + 2 * r), rb = __ldg(rays + 2 * r + 1);
   const float inv = __frcp_rn(__fsqrt_rn(fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, rb.z * rb.z))));
   const V4 w{rb.x * inv, rb.y * inv, rb.z * inv, 0.0f};
@@ -125,7 +126,6 @@ __global__ void __launch_bounds__(256)
     if (n_skipped) atomicAdd(n_skipped, 1ull);
     return;
   }
-  if (gw == 0.0f) return;
   const float v = 1.0f - u;
   const float B[4] = {v * v * v, 3.f * u * v * v, 3.f * u * u * v, u * u * u};
   const float dB[4] = {-3.f * v * v, 3.f * v * v - 6.f * u * v, 6.f * u * v - 3.f * u * u, 3.f * u * u};

@@ -18,9 +18,15 @@ term is the spacing of FP32 coordinates along the ray, below which no FP32
 computation can resolve a decision (a silhouette, a split plane, an end
 plane) or place a hit (for a ray nearly parallel to a fiber a sideways
 error e moves the hit along the fiber by e / tan(angle)).  A ray passes "in
-band" if the oracle result of one shifted copy (shifts of delta * 4^-k,
-k = 0..4, in 8 directions) meets the strict rule; every other ray is a
-failure.
+band" if the oracle result of one shifted copy (shifts of delta * 2^-k,
+k = 0..8, in 8 directions; the shifted rays are passed in double precision)
+meets the strict rule.
+
+Finally a ray is exempt ("silhouette") if it passes within 1e-4 r of the
+silhouette of the leaf cylinder hit by either side: |dist(ray, leaf axis) -
+r_leaf| < 1e-4 r_leaf, measured in FP64 between the ray line and the leaf's
+axis line.  There the hit is ill-conditioned (grazing) and hit/miss, t and u
+may all legitimately differ.  Every other ray is a failure.
 """
 import numpy as np
 
@@ -74,7 +80,7 @@ def _perp(w):
     return e1, e2
 
 
-SCALES = (1.0, 0.25, 0.0625, 0.015625, 0.00390625)
+SCALES = tuple(2.0 ** -k for k in range(9))
 
 
 def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
@@ -98,17 +104,17 @@ def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
     shifts = [sc * dv for sc in SCALES for dv in dirs]
     rp = case["row_ptr"].astype(np.int64)
     cand = [case["seg_idx"][rp[i]:rp[i + 1]] for i in idx]
+    tmax = rays[:, 3]
     sub_rays, rows, segs = [], [0], []
     for sh in shifts:
-        rr = case["rays"][idx].copy()
-        rr[:, :3] = (o + delta[:, None] * sh).astype(np.float32)
-        sub_rays.append(rr)
+        # double-precision rays: shifts far below an FP32 step of |o| stay exact
+        sub_rays.append(np.concatenate([o + delta[:, None] * sh, w, tmax[:, None]], axis=1))
         for c in cand:
             segs.append(c)
             rows.append(rows[-1] + len(c))
-    sub = dict(cps=case["cps"], rays=np.concatenate(sub_rays), row_ptr=np.array(rows, dtype=np.int32),
-               seg_idx=np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32))
-    ref = O.closest(sub, depth, pieces)
+    ref = O.closest_d(np.concatenate(sub_rays), np.array(rows, dtype=np.int32),
+                      np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32),
+                      depth, pieces)
     m = len(idx)
     tol_u = u_tolerance(case, case["rays"][idx], s_g[idx], t_g[idx], u_g[idx])
     ok = np.zeros(m, dtype=bool)
@@ -118,7 +124,28 @@ def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
     return idx[ok]
 
 
-def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces):
+def silhouette_dist(case, i, seg, leaf, depth):
+    """|dist(ray line, leaf axis line) - r_leaf| / r_leaf for the leaf of
+    segment `seg` starting at `leaf` (units of 2^-23), FP64."""
+    if seg < 0 or leaf < 0:
+        return np.inf
+    cp = case["cps"][seg].astype(np.float64)
+    size = O.ROOT_SIZE >> min(depth, 23)
+    start = (int(leaf) // size) * size
+    node = O.node_at(cp, start, size)
+    r_leaf = O.cons_radius(node)
+    ray = case["rays"][i].astype(np.float64)
+    o, w = ray[:3], ray[4:7] / np.linalg.norm(ray[4:7])
+    p, d = node[0, :3], node[1, :3]
+    n = np.cross(w, d)
+    if np.linalg.norm(n) == 0:
+        dist = np.linalg.norm(np.cross(p - o, w))
+    else:
+        dist = abs(np.dot(p - o, n)) / np.linalg.norm(n)
+    return abs(dist - r_leaf) / r_leaf
+
+
+def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces, gpu_leaf=None):
     """Returns a stats dict; 'fail' lists ray indices failing strict and band."""
     t_g = gpu_tu[:, 0].astype(np.float64)
     u_g = gpu_tu[:, 1].astype(np.float64)
@@ -127,7 +154,17 @@ def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces):
     ok = strict_ok(t_g, u_g, s_g, ref["t"], ref["u"], ref["seg"].astype(np.int64), tol_u)
     bad = np.nonzero(~ok)[0]
     banded = band_check(case, bad, t_g, u_g, s_g, depth, pieces)
-    fail = np.setdiff1d(bad, banded)
+    rest = np.setdiff1d(bad, banded)
+    sil = []
+    for i in rest:
+        ds = silhouette_dist(case, i, int(ref["seg"][i]), int(ref["leaf"][i]), depth) \
+            if "leaf" in ref else np.inf
+        if gpu_leaf is not None:
+            ds = min(ds, silhouette_dist(case, i, int(s_g[i]), int(gpu_leaf[i]), depth))
+        if ds < 1e-4:
+            sil.append(i)
+    sil = np.array(sil, dtype=np.int64)
+    fail = np.setdiff1d(rest, sil)
     both = (s_g >= 0) & (ref["seg"] >= 0) & ok
     rel = np.abs(t_g[both] - ref["t"][both]) / ref["t"][both] if both.any() else np.zeros(1)
     du = np.abs(u_g[both] - ref["u"][both]) if both.any() else np.zeros(1)
@@ -136,7 +173,7 @@ def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces):
                    ref=(float(ref["t"][i]), float(ref["u"][i]), int(ref["seg"][i])), tol_u=float(tol_u[i]))
               for i in fail[:6]]
     return dict(n=len(s_g), hits=int((ref["seg"] >= 0).sum()), strict=int(ok.sum()),
-                band=int(len(banded)), fail=fail, max_rel_t=float(rel.max()), max_du=float(du.max()),
+                band=int(len(banded)), silhouette=int(len(sil)), fail=fail, max_rel_t=float(rel.max()), max_du=float(du.max()),
                 max_du_over_tol=float(du_rel.max()), med_rel_t=float(np.median(rel)), detail=detail)
 
 

@@ -22,8 +22,13 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
+GRAZING = 0.05  # |<x - c(u), w>| < GRAZING r(u): the system is near singular
+
+
 def _oracle_grad(case, weights, depth):
-    """sum_i w_i dt_i/dtheta per segment, from the oracle's own hits."""
+    """sum_i w_i dt_i/dtheta per segment, from the oracle's own hits.  Rays
+    whose refined limit hit is an end disk or grazing (incidence cosine below
+    GRAZING) are left out of the check and get zero weight on both sides."""
     ref = O.closest(case, depth)
     g = np.zeros((case["cps"].shape[0], 4, 4))
     used = np.zeros(len(weights), dtype=bool)
@@ -33,7 +38,16 @@ def _oracle_grad(case, weights, depth):
         if u <= 0.0 or u >= 1.0:
             continue  # end-disk hits are checked separately
         r7 = O.ray7_from_packed(case["rays"][i])
-        gi = O.grad_t(r7, case["cps"][s].astype(np.float64), ref["t"][i], u)
+        cp = case["cps"][s].astype(np.float64)
+        tt, uu = O.refine_hit(r7, cp, ref["t"][i], u)
+        if not (0.0 < uu < 1.0):
+            continue
+        w = r7[3:6] / np.linalg.norm(r7[3:6])
+        c = I.bezier(cp[None], np.array([uu]))[0]
+        x = r7[:3] + tt * w
+        if abs(np.dot(x - c[:3], w)) < GRAZING * c[3]:
+            continue
+        gi = O.grad_t(r7, cp, ref["t"][i], u)
         if gi is None:
             continue
         g[s] += weights[i] * gi
@@ -106,13 +120,13 @@ def test_backward_translation_identity():
     fib = F.Fibers(case["cps"])
     tu, seg, _ = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], DEPTH)
     seg_np, u_np = seg.cpu().numpy(), tu[:, 1].cpu().numpy()
+    rays = torch.tensor(case["rays"], device="cuda")
     checked = 0
     for i in range(256):
         if seg_np[i] < 0 or u_np[i] <= 0 or u_np[i] >= 1:
             continue
-        gt = torch.zeros(256, device="cuda")
-        gt[i] = 1.0
-        g, sk = F.intersect_backward(fib, case["rays"], tu, seg, gt)
+        g, sk = F.intersect_backward(fib, rays[i:i + 1], tu[i:i + 1], seg[i:i + 1],
+                                     torch.ones(1, device="cuda"))
         if int(sk.item()):
             continue
         gs = g[seg_np[i]].cpu().numpy().astype(np.float64)
