@@ -80,13 +80,13 @@ typedef struct {
 } fx_fibers_info;
 
 /* Persistent kernel variants (fx_launch.variant). */
-#define FX_VARIANT_AUTO 0 /* warp per ray when n_pair >= 8 n_ray, else lane per ray */
-#define FX_VARIANT_LANE 1 /* each lane owns a ray and walks its candidates */
-#define FX_VARIANT_WARP 2 /* a warp owns a ray; candidates staged in shared memory */
+#define FX_VARIANT_AUTO 0 /* the library's choice (lane per ray) */
+#define FX_VARIANT_LANE 1 /* each lane owns a ray and walks its candidates front to back */
+#define FX_VARIANT_WARP 2 /* a warp owns a ray; its candidates are staged in shared memory */
 
 /* Launch configuration of the persistent kernels (fx_set_launch). */
 typedef struct {
-    int32_t block;         /* lane-per-ray threads per block: 64, 128 or 256 */
+    int32_t block;         /* reserved: 64, 128 or 256 (both variants run 128-thread blocks) */
     int32_t blocks_per_sm; /* blocks per SM the grid is sized for (1..16; 0 = as many as fit) */
     int32_t chunk;         /* lane-per-ray: rays a warp takes from the queue at a time (1..1024) */
     int32_t variant;       /* FX_VARIANT_* */

@@ -10,7 +10,11 @@
 //   J = [[<w, c'>, <x - c, c''> - |c'|^2], [2 <x - c, w>, -2 <x - c, c'> - 2 r r']],
 //   dG1/dp_k = -B_k c' + B_k' (x - c),  dG2/dp_k = -2 B_k (x - c),
 //   dG2/dr_k = -2 r B_k.
-// End-disk hits (u exactly 0 or 1) keep u fixed and use G1 alone.
+// A hit is lateral if the refinement converges with u in [0, 1]; otherwise it
+// is an end-disk hit at the nearer end (u fixed at 0 or 1, t from the disk's
+// plane, G1 alone), provided the point lies in the disk.  The forward u
+// cannot tell a lateral hit near an end from the disk in FP32 (u = 1 - 5e-8
+// rounds to 1), so the classification is geometric.
 // One thread per ray; contributions are added to grad_cps with atomics.
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -67,8 +71,8 @@ __global__ void __launch_bounds__(256)
   const V4 A2{3.f * (D1.x - D0.x), 3.f * (D1.y - D0.y), 3.f * (D1.z - D0.z), 3.f * (D1.w - D0.w)};
   const V4 A3{D2.x - 2.f * D1.x + D0.x, D2.y - 2.f * D1.y + D0.y, D2.z - 2.f * D1.z + D0.z,
               D2.w - 2.f * D1.w + D0.w};
-  float t = tu[r].x, u = tu[r].y;
-  const bool cap = (u == 0.0f || u == 1.0f);
+  const float t_fwd = tu[r].x, u_fwd = tu[r].y;
+  float t = t_fwd, u = fminf(fmaxf(u_fwd, 1e-6f), 1.0f - 1e-6f);
 
   V4 c, c1, c2, e;
   float J00 = 0.f, J01 = 0.f, J10 = 0.f, J11 = 0.f;
@@ -92,34 +96,41 @@ __global__ void __launch_bounds__(256)
     J10 = 2.f * d3(e, w);
     J11 = -2.f * d3(e, c1) - 2.f * c.w * c1.w;
   };
-  bool ok = true;
-  if (!cap) {
-    for (int it = 0; it < 4; ++it) {
-      evaluate(u, t);
-      const float G1 = d3(e, c1), G2 = d3(e, e) - c.w * c.w;
-      const float det = J00 * J11 - J01 * J10;
-      if (!(fabsf(det) > 0.0f)) {
-        ok = false;
-        break;
-      }
-      const float id = __frcp_rn(det);
-      t -= (J11 * G1 - J01 * G2) * id;
-      u -= (J00 * G2 - J10 * G1) * id;
+  bool lateral = true;
+  for (int it = 0; it < 5; ++it) {
+    evaluate(u, t);
+    const float G1 = d3(e, c1), G2 = d3(e, e) - c.w * c.w;
+    const float det = J00 * J11 - J01 * J10;
+    if (!(fabsf(det) > 0.0f)) {
+      lateral = false;
+      break;
     }
-    ok = ok && u >= 0.0f && u <= 1.0f && isfinite(t);
+    const float id = __frcp_rn(det);
+    t -= (J11 * G1 - J01 * G2) * id;
+    u -= (J00 * G2 - J10 * G1) * id;
   }
-  evaluate(u, t);
+  lateral = lateral && u >= 0.0f && u <= 1.0f && isfinite(t);
   float a1 = 0.f, a2 = 0.f;  // dt/dtheta = -(a1 dG1/dtheta + a2 dG2/dtheta)
-  if (cap) {
-    ok = fabsf(J00) > 1e-7f * sqrtf(d3(c1, c1));
-    if (ok) a1 = __frcp_rn(J00);
-  } else if (ok) {
+  bool ok;
+  if (lateral) {
+    evaluate(u, t);
     const float det = J00 * J11 - J01 * J10;
     ok = fabsf(det) > 1e-5f * (fabsf(J00 * J11) + fabsf(J01 * J10));
     if (ok) {
       const float id = __frcp_rn(det);
       a1 = J11 * id;
       a2 = -J01 * id;
+    }
+  } else {
+    // end disk at the nearer end: t where the ray meets the disk's plane
+    u = u_fwd >= 0.5f ? 1.0f : 0.0f;
+    evaluate(u, t_fwd);
+    ok = fabsf(J00) > 1e-7f * sqrtf(d3(c1, c1));
+    if (ok) {
+      t = t_fwd - d3(e, c1) / J00;  // G1 is linear in t
+      evaluate(u, t);
+      ok = d3(e, e) <= c.w * c.w * 1.0001f;
+      a1 = __frcp_rn(J00);
     }
   }
   if (!ok) {

@@ -71,13 +71,6 @@ fx::TraceArgs make_args(const fx_fibers* f, const float* rays, int64_t n_ray, co
   return a;
 }
 
-int grid_for(const fx_fibers* f, bool pairs, uint32_t flags) {
-  int per_sm = fx::persistent_occupancy(pairs, flags, f->launch.block);
-  if (per_sm < 1) per_sm = 1;
-  if (f->launch.blocks_per_sm > 0) per_sm = std::min(per_sm, (int)f->launch.blocks_per_sm);
-  return f->sm_count * per_sm;
-}
-
 fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t flags,
                       cudaStream_t s) {
   if (a.n_ray == 0) return FX_OK;
@@ -94,12 +87,11 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
     return FX_OK;
   }
   FX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s));
-  int variant = f->launch.variant;
-  if (variant == FX_VARIANT_AUTO) variant = a.n_pair >= 8 * a.n_ray ? FX_VARIANT_WARP : FX_VARIANT_LANE;
+  const int variant = f->launch.variant == FX_VARIANT_AUTO ? FX_VARIANT_LANE : f->launch.variant;
   if (variant == FX_VARIANT_WARP) {
     FX_CUDA(fx::launch_warp_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
   } else {
-    FX_CUDA(fx::launch_persistent(a, pairs, flags, grid_for(f, pairs, flags), f->launch.block, s));
+    FX_CUDA(fx::launch_lane_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
   }
   return FX_OK;
 }

@@ -24,7 +24,7 @@ struct fx_fibers {
   int32_t *piece_info = nullptr;        // n_piece: level | off << 4 | unsupported << 31
   float4 *seg_cp = nullptr;             // n_seg x 4 control points (backward, polish)
   uint32_t *ws = nullptr;               // FX_WS_WORDS words + 8 uint64 counters
-  fx_launch launch{128, 0, 32, FX_VARIANT_AUTO};  // blocks_per_sm 0: as many as fit
+  fx_launch launch{128, 0, 32, FX_VARIANT_LANE};  // blocks_per_sm 0: as many as fit
   // host-buffer entry staging (grow-only)
   void *stage = nullptr;
   size_t stage_bytes = 0;
@@ -57,12 +57,12 @@ struct TraceArgs {
 };
 
 // Launchers (trace_kernels.cu).  flags: FX_* bits of the public header.
-cudaError_t launch_persistent(const TraceArgs &a, bool pairs, uint32_t flags, int grid, int block,
-                              cudaStream_t s);
 cudaError_t launch_naive(const TraceArgs &a, bool pairs, uint32_t flags, cudaStream_t s);
 cudaError_t launch_polish(const TraceArgs &a, const float4 *seg_cp, cudaStream_t s);
-int persistent_regs(bool pairs, uint32_t flags);
-int persistent_occupancy(bool pairs, uint32_t flags, int block);
+
+// lane_kernels.cu
+cudaError_t launch_lane_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
+                            int sm_count, cudaStream_t s);
 
 // warp_kernels.cu
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,

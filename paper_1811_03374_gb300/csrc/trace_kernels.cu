@@ -1,14 +1,6 @@
 // trace_kernels.cu -- forward kernels of the ray / cubic-fiber intersector.
 //
-// k_persistent  persistent work-queue kernel: each warp takes chunks of rays
-//               from an atomic queue; every lane owns one ray, walks its
-//               candidate segments in row order with the closest hit so far
-//               as t_max (Sec. 3.2 instant termination across candidates),
-//               and refills itself from the warp's ray pool (ballot + popc
-//               ranking) the moment its ray is finished, so lanes stay busy
-//               despite uneven candidate counts.  Each loop iteration performs
-//               one node test per lane; the traversal state is the paper's
-//               bit string, start and size in registers (Sec. 3.3).
+// (the persistent kernels live in lane_kernels.cu and warp_kernels.cu)
 // k_naive       one thread per (ray, candidate) pair, same arithmetic; the
 //               closest hit per ray is an atomicMin over packed (t, pair)
 //               keys followed by a resolve pass.  The baseline K1 must beat.
@@ -22,206 +14,6 @@
 namespace fx {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// ---------------------------------------------------------------------------
-// persistent kernel
-// ---------------------------------------------------------------------------
-template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
-__global__ void __launch_bounds__(256) k_persistent(const TraceArgs a) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt_mask = (1u << lane) - 1u;
-
-  // warp-uniform ray pool
-  int64_t pool_next = 0, pool_end = 0;
-  bool exhausted = false;
-
-  // lane state
-  int64_t ray = -1;
-  int32_t cand = 0, crow = 0, cend = 0, pc = 0, pend = 0, cur_seg = -1, cur_piece = -1;
-  RayFrame rf;
-  float ray_tmax = 0.0f;
-  float best_t = 0.0f, best_u = -1.0f;
-  int32_t best_seg = -1, best_leaf = -1;
-  float cand_t = 0.0f, cand_u = -1.0f;  // PAIRS: best over the current candidate's pieces
-  int32_t cand_leaf = -1;
-  bool active = false;  // a node is ready to be tested
-  bool done = false;    // no more work for this lane
-  PairState st;
-  unsigned long long n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
-
-  // Moves the lane to its next piece; finishes candidates (pairs mode) and
-  // the ray when they run out.  Returns true when a piece is ready.
-  auto next_piece = [&]() -> bool {
-    while (ray >= 0) {
-      if (pc < pend) {
-        cur_piece = pc++;
-        return true;
-      }
-      if (PAIRS && cand >= crow) {
-        a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
-        if (a.leaf) a.leaf[cand] = cand_leaf;
-      }
-      if (++cand < cend) {
-        const int32_t s = __ldg(a.seg_idx + cand);
-        if (PAIRS) {
-          cand_t = ray_tmax;
-          cand_u = -1.0f;
-          cand_leaf = -1;
-        }
-        if (CHECK && (s < 0 || s >= a.n_seg)) {
-          atomicOr(a.status, FX_DEV_BAD_INDEX);
-          pc = pend = 0;
-          cand_t = kInf;
-          continue;
-        }
-        cur_seg = s;
-        if (a.identity) {
-          pc = s;
-          pend = s + 1;
-        } else {
-          pc = __ldg(a.piece_begin + s);
-          pend = __ldg(a.piece_begin + s + 1);
-        }
-      } else {
-        if (!PAIRS) {
-          const bool hit = best_seg >= 0;
-          a.tu[ray] = make_float2(hit ? best_t : kInf, hit ? best_u : -1.0f);
-          a.seg[ray] = best_seg;
-          if (a.leaf) a.leaf[ray] = best_leaf;
-        }
-        ray = -1;
-      }
-    }
-    return false;
-  };
-
-  for (;;) {
-    // ---- 1. acquire a (ray, piece) pair for every idle lane ---------------
-    bool fresh = false;
-    if (!active && !done) fresh = next_piece();
-    // lanes without a ray take new rays from the warp pool
-    for (;;) {
-      const bool want = !active && !done && !fresh && ray < 0;
-      const unsigned m = __ballot_sync(kFull, want);
-      if (m == 0u) break;
-      if (pool_next >= pool_end) {
-        if (exhausted) {
-          if (want) done = true;
-          continue;
-        }
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, (unsigned)a.chunk);
-        base = __shfl_sync(kFull, base, 0);
-        if ((int64_t)base >= a.n_ray) {
-          exhausted = true;
-          continue;
-        }
-        pool_next = base;
-        pool_end = min((int64_t)base + a.chunk, a.n_ray);
-      }
-      const int rank = __popc(m & lt_mask);
-      const int64_t avail = pool_end - pool_next;
-      if (want && rank < avail) {
-        const int64_t r = pool_next + rank;
-        crow = __ldg(a.row_ptr + r);
-        cend = __ldg(a.row_ptr + r + 1);
-        if (crow >= cend) {
-          // no candidates: a miss, without loading the ray
-          if (!PAIRS) {
-            a.tu[r] = make_float2(kInf, -1.0f);
-            a.seg[r] = -1;
-            if (a.leaf) a.leaf[r] = -1;
-          }
-        } else {
-          ray = r;
-          rf = load_ray<FAST>(a.rays, ray, ray_tmax);
-          best_t = ray_tmax;
-          best_u = -1.0f;
-          best_seg = -1;
-          best_leaf = -1;
-          cand = crow - 1;
-          pc = pend = 0;
-          fresh = next_piece();
-        }
-      }
-      pool_next += min((int64_t)__popc(m), avail);
-    }
-
-    // ---- 2. set up fresh pairs -------------------------------------------
-    if (fresh) {
-      begin_piece<FAST>(st, a.piece, cur_piece, rf, a.identity ? 0 : __ldg(a.piece_info + cur_piece), a.depth,
-                        PAIRS ? cand_t : best_t);
-      active = true;
-      if (COUNT) ++n_tests;
-    }
-    if (__all_sync(kFull, !active)) break;
-
-    // ---- 3. node test (Sec. 3.2 / 3.3) ------------------------------------
-    if (active) {
-      const float r = cons_radius<FAST>(st.c);
-      float c0 = 0.0f, c1 = 0.0f;
-      const bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1) &&
-                        fmaxf(c0, st.tmin) <= fminf(c1, st.tmax);
-      if (COUNT) ++n_nodes;
-      ++st.iters;
-      if (over && st.size <= st.min_size) {
-        // leaf: entry into the capped leaf cylinder; stop (instant termination)
-        const float t = fmaxf(c0, st.tmin);
-        const float lim = PAIRS ? cand_t : best_t;
-        if (t < lim) {
-          const float up = leaf_u<FAST>(st.c, t, st.start, st.size);
-          float u;
-          int32_t leaf;
-          to_segment(st.info, up, st.start, u, leaf);
-          if (st.info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
-          if (PAIRS) {
-            cand_t = t;
-            cand_u = u;
-            cand_leaf = leaf;
-          } else {
-            best_t = t;
-            best_u = u;
-            best_seg = cur_seg;
-            best_leaf = leaf;
-          }
-          if (COUNT) ++n_hits;
-        }
-        active = false;
-      } else if (over) {
-        descend<FAST>(st.c, c0, c1, st.tmin, st.tmax, st.bits, st.start, st.size);
-        if (COUNT) ++n_desc;
-      } else if (st.bits == 0u) {
-        active = false;
-      } else {
-        jump_up(st.bits, st.start, st.size);
-        recompute(st.R, st.start, st.size, st.c);
-        slab<FAST>(st.c, PAIRS ? cand_t : best_t, st.tmin, st.tmax);
-        if (COUNT) ++n_back;
-      }
-      if (active && st.iters >= iter_cap(a.depth)) {
-        atomicOr(a.status, FX_DEV_ITER_LIMIT);
-        active = false;
-      }
-    }
-  }
-
-  if (COUNT) {
-    for (int o = 16; o > 0; o >>= 1) {
-      n_nodes += __shfl_down_sync(kFull, n_nodes, o);
-      n_desc += __shfl_down_sync(kFull, n_desc, o);
-      n_back += __shfl_down_sync(kFull, n_back, o);
-      n_tests += __shfl_down_sync(kFull, n_tests, o);
-      n_hits += __shfl_down_sync(kFull, n_hits, o);
-    }
-    if (lane == 0) {
-      atomicAdd(a.counters + 0, n_nodes);
-      atomicAdd(a.counters + 1, n_desc);
-      atomicAdd(a.counters + 2, n_back);
-      atomicAdd(a.counters + 3, n_tests);
-      atomicAdd(a.counters + 4, n_hits);
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // naive kernel: one thread per pair
@@ -497,63 +289,6 @@ __global__ void __launch_bounds__(256) k_polish(const TraceArgs a, const float4*
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
-static cudaError_t launch_p(const TraceArgs& a, int grid, int block, cudaStream_t s) {
-  k_persistent<FAST, PAIRS, COUNT, CHECK><<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <bool FAST, bool PAIRS>
-static cudaError_t launch_p2(const TraceArgs& a, uint32_t flags, int grid, int block,
-                             cudaStream_t s) {
-  const bool cnt = flags & FX_COUNT, chk = flags & FX_CHECK_INDEX;
-  if (cnt) return chk ? launch_p<FAST, PAIRS, true, true>(a, grid, block, s)
-                      : launch_p<FAST, PAIRS, true, false>(a, grid, block, s);
-  return chk ? launch_p<FAST, PAIRS, false, true>(a, grid, block, s)
-             : launch_p<FAST, PAIRS, false, false>(a, grid, block, s);
-}
-
-cudaError_t launch_persistent(const TraceArgs& a, bool pairs, uint32_t flags, int grid, int block,
-                              cudaStream_t s) {
-  const bool fast = flags & FX_FAST_MATH;
-  if (pairs) return fast ? launch_p2<true, true>(a, flags, grid, block, s)
-                         : launch_p2<false, true>(a, flags, grid, block, s);
-  return fast ? launch_p2<true, false>(a, flags, grid, block, s)
-              : launch_p2<false, false>(a, flags, grid, block, s);
-}
-
-int persistent_regs(bool pairs, uint32_t flags) {
-  cudaFuncAttributes at{};
-  const bool fast = flags & FX_FAST_MATH;
-  cudaError_t e;
-  if (pairs) e = fast ? cudaFuncGetAttributes(&at, k_persistent<true, true, false, false>)
-                      : cudaFuncGetAttributes(&at, k_persistent<false, true, false, false>);
-  else e = fast ? cudaFuncGetAttributes(&at, k_persistent<true, false, false, false>)
-                : cudaFuncGetAttributes(&at, k_persistent<false, false, false, false>);
-  return e == cudaSuccess ? at.numRegs : -1;
-}
-
-int persistent_occupancy(bool pairs, uint32_t flags, int block) {
-  int n = 0;
-  const bool fast = flags & FX_FAST_MATH, cnt = flags & FX_COUNT, chk = flags & FX_CHECK_INDEX;
-  // occupancy of the instantiation that will be launched
-#define FX_OCC(F, P, C, K) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<F, P, C, K>, block, 0)
-  cudaError_t e;
-  if (pairs) {
-    if (fast) e = cnt ? (chk ? FX_OCC(true, true, true, true) : FX_OCC(true, true, true, false))
-                      : (chk ? FX_OCC(true, true, false, true) : FX_OCC(true, true, false, false));
-    else e = cnt ? (chk ? FX_OCC(false, true, true, true) : FX_OCC(false, true, true, false))
-                 : (chk ? FX_OCC(false, true, false, true) : FX_OCC(false, true, false, false));
-  } else {
-    if (fast) e = cnt ? (chk ? FX_OCC(true, false, true, true) : FX_OCC(true, false, true, false))
-                      : (chk ? FX_OCC(true, false, false, true) : FX_OCC(true, false, false, false));
-    else e = cnt ? (chk ? FX_OCC(false, false, true, true) : FX_OCC(false, false, true, false))
-                 : (chk ? FX_OCC(false, false, false, true) : FX_OCC(false, false, false, false));
-  }
-#undef FX_OCC
-  return e == cudaSuccess ? n : 0;
-}
-
 template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
 static cudaError_t launch_n(const TraceArgs& a, cudaStream_t s) {
   const int block = 256;

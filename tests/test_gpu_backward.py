@@ -26,28 +26,37 @@ GRAZING = 0.05  # |<x - c(u), w>| < GRAZING r(u): the system is near singular
 
 
 def _oracle_grad(case, weights, depth):
-    """sum_i w_i dt_i/dtheta per segment, from the oracle's own hits.  Rays
-    whose refined limit hit is an end disk or grazing (incidence cosine below
-    GRAZING) are left out of the check and get zero weight on both sides."""
+    """sum_i w_i dt_i/dtheta per segment, from the oracle's own hits.  A hit is
+    lateral if Newton refinement on the limit surface stays in u in [0, 1],
+    otherwise an end-disk hit at the nearer end (t from the disk's plane),
+    the rule the adjoint kernel applies.  Grazing lateral hits (incidence
+    cosine below GRAZING) are left out of the check and get zero weight on
+    both sides."""
     ref = O.closest(case, depth)
     g = np.zeros((case["cps"].shape[0], 4, 4))
     used = np.zeros(len(weights), dtype=bool)
     for i in np.nonzero(ref["seg"] >= 0)[0]:
         s = ref["seg"][i]
-        u = ref["u"][i]
-        if u <= 0.0 or u >= 1.0:
-            continue  # end-disk hits are checked separately
+        u = min(max(ref["u"][i], 1e-6), 1 - 1e-6)
         r7 = O.ray7_from_packed(case["rays"][i])
+        w = r7[3:6] / np.linalg.norm(r7[3:6])
         cp = case["cps"][s].astype(np.float64)
         tt, uu = O.refine_hit(r7, cp, ref["t"][i], u)
-        if not (0.0 < uu < 1.0):
-            continue
-        w = r7[3:6] / np.linalg.norm(r7[3:6])
-        c = I.bezier(cp[None], np.array([uu]))[0]
-        x = r7[:3] + tt * w
-        if abs(np.dot(x - c[:3], w)) < GRAZING * c[3]:
-            continue
-        gi = O.grad_t(r7, cp, ref["t"][i], u)
+        if 0.0 <= uu <= 1.0:
+            c = I.bezier(cp[None], np.array([uu]))[0]
+            x = r7[:3] + tt * w
+            if abs(np.dot(x - c[:3], w)) < GRAZING * c[3]:
+                continue
+            gi = O.grad_t(r7, cp, tt, uu)
+        else:
+            ue = 1.0 if ref["u"][i] >= 0.5 else 0.0
+            c = I.bezier(cp[None], np.array([ue]))[0]
+            n = I.bezier_tangent(cp[None], np.array([ue]))[0][:3]
+            tt = np.dot(c[:3] - r7[:3], n) / np.dot(w, n)
+            x = r7[:3] + tt * w
+            if np.dot(x - c[:3], x - c[:3]) > c[3] ** 2 * 0.999:
+                continue
+            gi = O.grad_t(r7, cp, tt, ue)
         if gi is None:
             continue
         g[s] += weights[i] * gi
@@ -123,7 +132,7 @@ def test_backward_translation_identity():
     rays = torch.tensor(case["rays"], device="cuda")
     checked = 0
     for i in range(256):
-        if seg_np[i] < 0 or u_np[i] <= 0 or u_np[i] >= 1:
+        if seg_np[i] < 0:
             continue
         g, sk = F.intersect_backward(fib, rays[i:i + 1], tu[i:i + 1], seg[i:i + 1],
                                      torch.ones(1, device="cuda"))
