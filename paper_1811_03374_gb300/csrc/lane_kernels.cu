@@ -11,11 +11,14 @@
 // (Sec. 3.3).
 //
 // Latency of the per-candidate gathers is taken off the critical path by a
-// per-lane software pipeline: the piece (64 B) of the next candidate is copied
-// into the lane's shared-memory slot with cp.async while the current one is
-// traversed, and segment ids are loaded two candidates ahead.  The root node
-// kept for backtracking lives in shared memory, and the slab (two plane
-// divisions) of a node is formed only once its cylinder is hit.
+// per-lane software pipeline: the piece (64 B) and its root radius of the next
+// candidate are copied into the lane's shared-memory slot with cp.async while
+// the current one is traversed, and segment ids are loaded two candidates
+// ahead.  Most candidates miss their root cylinder, so the root test needs
+// only p and d in the ray frame and the piece's precomputed root radius (a
+// rigid motion does not change it); t0, t1 are rotated, the root node saved
+// for backtracking (in shared memory) and the slab (two plane divisions)
+// formed only once that cylinder is hit.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -43,7 +46,9 @@ struct Lite {  // traversal state kept in registers (the root node is in shared 
   float tmin, tmax;
   uint32_t bits, start, size, min_size;
   int32_t info, iters;
-  bool slab_ok;
+  float root_r;   // precomputed radius of the root cylinder
+  bool slab_ok;   // tmin / tmax hold the current node's slab
+  bool at_root;   // t0, t1 not yet rotated (still in the lane's slot)
 };
 
 template <bool FAST>
@@ -56,8 +61,9 @@ __device__ __forceinline__ void to_local(const float4& p, const float4& d, const
 }
 
 template <bool FAST, bool PAIRS, bool COUNT, bool IDENTITY>
-__global__ void __launch_bounds__(kLaneBlock) k_lane(const TraceArgs a, int check) {
+__global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int check) {
   __shared__ __align__(16) float4 s_slot[2][4][kLaneBlock];  // [parity][component][lane]
+  __shared__ float s_rad[2][kLaneBlock];
   __shared__ __align__(16) float4 s_root[4][kLaneBlock];
   const int tid = threadIdx.x, lane = tid & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -78,32 +84,28 @@ __global__ void __launch_bounds__(kLaneBlock) k_lane(const TraceArgs a, int chec
   Lite st;
   uint32_t n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
 
-  auto seg_at = [&](int32_t j) -> int32_t {
-    if (j >= cend) return -1;
-    const int32_t s = __ldg(a.seg_idx + j);
-    if (check && (s < 0 || s >= a.n_seg)) {
-      atomicOr(a.status, FX_DEV_BAD_INDEX);
-      return -2;
-    }
-    return s;
+  // Loaded ids are checked only where they are used (one and two candidates
+  // later), so the loads stay off the critical path.
+  auto seg_at = [&](int32_t j) -> int32_t { return j < cend ? __ldg(a.seg_idx + j) : -1; };
+  auto valid = [&](int32_t s) -> bool {
+    if (s < 0) return false;
+    if (check && s >= a.n_seg) return false;
+    return true;
   };
   auto prefetch = [&](int32_t s, int parity) {
-    if (IDENTITY && s >= 0) {
+    if (IDENTITY && valid(s)) {
       const float4* src = a.piece + 4 * (int64_t)s;
       cp16(&s_slot[parity][0][tid], src);
       cp16(&s_slot[parity][1][tid], src + 1);
       cp16(&s_slot[parity][2][tid], src + 2);
       cp16(&s_slot[parity][3][tid], src + 3);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr(&s_rad[parity][tid])),
+                   "l"(a.piece_rad + s)
+                   : "memory");
     }
     commit();
   };
-  // Starts the test of piece k (data in registers) for the current candidate.
-  auto begin = [&](const float4& p, const float4& d, const float4& t0, const float4& t1, int32_t info) {
-    to_local<FAST>(p, d, t0, t1, rf, st.c);
-    s_root[0][tid] = st.c.p;
-    s_root[1][tid] = st.c.d;
-    s_root[2][tid] = st.c.t0;
-    s_root[3][tid] = st.c.t1;
+  auto init_state = [&](int32_t info) {
     st.bits = 0;
     st.start = 0;
     st.size = kRootSize;
@@ -115,9 +117,26 @@ __global__ void __launch_bounds__(kLaneBlock) k_lane(const TraceArgs a, int chec
     active = true;
     if (COUNT) ++n_tests;
   };
+  // Piece k from global memory, fully rotated (pre-split segments).
   auto begin_piece_k = [&](int32_t k) {
-    begin(__ldg(a.piece + 4 * (int64_t)k), __ldg(a.piece + 4 * (int64_t)k + 1),
-          __ldg(a.piece + 4 * (int64_t)k + 2), __ldg(a.piece + 4 * (int64_t)k + 3), __ldg(a.piece_info + k));
+    to_local<FAST>(__ldg(a.piece + 4 * (int64_t)k), __ldg(a.piece + 4 * (int64_t)k + 1),
+                   __ldg(a.piece + 4 * (int64_t)k + 2), __ldg(a.piece + 4 * (int64_t)k + 3), rf, st.c);
+    s_root[0][tid] = st.c.p;
+    s_root[1][tid] = st.c.d;
+    s_root[2][tid] = st.c.t0;
+    s_root[3][tid] = st.c.t1;
+    st.root_r = __ldg(a.piece_rad + k);
+    st.at_root = false;
+    init_state(__ldg(a.piece_info + k));
+  };
+  // Piece of the current candidate from the lane's slot: only p and d rotated.
+  auto begin_slot = [&](int par) {
+    const float4 p = s_slot[par][0][tid], d = s_slot[par][1][tid];
+    st.c.p = rotate(rf, p.x - rf.o.x, p.y - rf.o.y, p.z - rf.o.z, p.w);
+    st.c.d = rotate(rf, d.x, d.y, d.z, d.w);
+    st.root_r = s_rad[par][tid];
+    st.at_root = true;
+    init_state(0);
   };
   auto finish_candidate = [&]() {
     if (PAIRS) {
@@ -151,12 +170,15 @@ __global__ void __launch_bounds__(kLaneBlock) k_lane(const TraceArgs a, int chec
         cand_u = -1.0f;
         cand_leaf = -1;
       }
+      if (!valid(s_cur)) {
+        atomicOr(a.status, FX_DEV_BAD_INDEX);
+        s_cur = -1;
+      }
       if (IDENTITY) {
         prefetch(s_n1, (cand + 1) & 1);  // one group per candidate
         wait_all_but_one();              // this candidate's group has landed
         if (s_cur < 0) continue;
-        const int par = cand & 1;
-        begin(s_slot[par][0][tid], s_slot[par][1][tid], s_slot[par][2][tid], s_slot[par][3][tid], 0);
+        begin_slot(cand & 1);
         return;
       } else {
         if (s_cur < 0) continue;
@@ -224,9 +246,21 @@ __global__ void __launch_bounds__(kLaneBlock) k_lane(const TraceArgs a, int chec
     // ---- 2. one node step per active lane ----------------------------------
     if (active) {
       const float pair_tmax = PAIRS ? cand_t : best_t;
-      const float r = cons_radius<FAST>(st.c);
+      const float r = (st.iters == 0) ? st.root_r : cons_radius<FAST>(st.c);
       float c0 = 0.0f, c1 = 0.0f;
       bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1);
+      if (over && st.at_root) {
+        // the root cylinder is hit: rotate the tangents and keep the root node
+        const int par = cand & 1;
+        const float4 t0 = s_slot[par][2][tid], t1 = s_slot[par][3][tid];
+        st.c.t0 = rotate(rf, t0.x, t0.y, t0.z, t0.w);
+        st.c.t1 = rotate(rf, t1.x, t1.y, t1.z, t1.w);
+        s_root[0][tid] = st.c.p;
+        s_root[1][tid] = st.c.d;
+        s_root[2][tid] = st.c.t0;
+        s_root[3][tid] = st.c.t1;
+        st.at_root = false;
+      }
       if (over && !st.slab_ok) {
         const float lim = st.tmax;
         slab<FAST>(st.c, lim, st.tmin, st.tmax);

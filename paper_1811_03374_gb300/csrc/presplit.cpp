@@ -136,6 +136,23 @@ void emit(const Curve& c, int level, int off, bool ok, std::vector<PieceRec>& ou
     p.pdt[8 + k] = (float)t0.v[k];
     p.pdt[12 + k] = (float)t1.v[k];
   }
+  // conservative radius of the whole piece: the inner control points'
+  // distance from the chord plus the largest control radius (Sec. 3.3); a
+  // rigid motion leaves it unchanged, so it is the same in every ray frame
+  const double dd = dot(d, d);
+  double m = 0.0;
+  for (const P4* q : {&t0, &t1}) {
+    double l2 = dot(*q, *q);
+    if (dd > 0.0) {
+      const double b = dot(*q, d) / dd;
+      const P4 r = axpy(-b, d, *q);
+      l2 = dot(r, r);
+    }
+    m = std::max(m, l2);
+  }
+  double rmax = 0.0;
+  for (const P4& cpk : c) rmax = std::max(rmax, cpk.v[3]);
+  p.root_radius = (float)(std::sqrt(m) + rmax);
   p.level = level;
   p.off = off;
   p.unsupported = !ok;

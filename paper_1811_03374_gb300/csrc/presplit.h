@@ -8,6 +8,7 @@ namespace fx {
 
 struct PieceRec {
   float pdt[16];  // (p, d, t0, t1) x (x, y, z, r), world space
+  float root_radius;  // conservative radius of the piece's bounding cylinder (Sec. 3.3)
   int32_t level;  // pre-split level k (the piece is [off, off + 1] * 2^-k)
   int32_t off;
   bool unsupported;

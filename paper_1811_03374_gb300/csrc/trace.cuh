@@ -141,11 +141,12 @@ __device__ __forceinline__ bool cylinder(const float4& p, const float4& a, float
   const float h = frcp<FAST>(g);
   const float cr = fmaf(a.x, p.y, -a.y * p.x);
   const float e = fmaf(-cr * cr, h, r * r);
+  if (e < 0.0f) return false;
   const float tcpa = fmaf(-a.z * h, fmaf(a.x, p.x, a.y * p.y), p.z);
-  const float s = fsqrt<FAST>(fmaxf(e, 0.0f) * fmaf(a.z, a.z, g) * h);
+  const float s = fsqrt<FAST>(e * fmaf(a.z, a.z, g) * h);
   c0 = tcpa - s;
   c1 = tcpa + s;
-  return e >= 0.0f;
+  return true;
 }
 
 // t-interval between the start plane (through p, normal t0, kept side
