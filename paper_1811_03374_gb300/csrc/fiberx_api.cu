@@ -57,6 +57,7 @@ fx::TraceArgs make_args(const fx_fibers* f, const float* rays, int64_t n_ray, co
   a.piece_begin = f->piece_begin;
   a.piece_info = f->piece_info;
   a.piece_rad = f->piece_rad;
+  a.piece_root = f->piece_root;
   a.rays = reinterpret_cast<const float4*>(rays);
   a.row_ptr = row_ptr;
   a.seg_idx = seg_idx;
@@ -157,9 +158,16 @@ fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, c
   std::vector<float> packed(pieces.size() * 16);
   std::vector<int32_t> info(pieces.size());
   std::vector<float> rad(pieces.size());
+  std::vector<float> rootrec(pieces.size() * 8);
   for (size_t k = 0; k < pieces.size(); ++k) {
     std::memcpy(&packed[16 * k], pieces[k].pdt, sizeof(pieces[k].pdt));
     rad[k] = pieces[k].root_radius;
+    for (int a = 0; a < 3; ++a) {
+      rootrec[8 * k + a] = pieces[k].pdt[a];          // p
+      rootrec[8 * k + 4 + a] = pieces[k].pdt[4 + a];  // d
+    }
+    rootrec[8 * k + 3] = pieces[k].root_radius;
+    rootrec[8 * k + 7] = 0.0f;
     info[k] = pieces[k].level | (pieces[k].off << 4) | (pieces[k].unsupported ? (int32_t)0x80000000 : 0);
     f->max_level = std::max(f->max_level, pieces[k].level);
     if (pieces[k].unsupported) f->n_unsupported++;
@@ -179,6 +187,7 @@ fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, c
   if ((e = cudaMalloc((void**)&f->piece_info, np * 4)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc info");
   if ((e = cudaMalloc((void**)&f->seg_cp, ns * 64)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc seg_cp");
   if ((e = cudaMalloc((void**)&f->piece_rad, np * 4)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc rad");
+  if ((e = cudaMalloc((void**)&f->piece_root, np * 32)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc root");
   const size_t ws_bytes = FX_WS_WORDS * 4 + 8 * 8;
   if ((e = cudaMalloc((void**)&f->ws, ws_bytes)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc ws");
   if ((e = cudaMemsetAsync(f->ws, 0, ws_bytes, s)) != cudaSuccess) return cleanup(FX_ECUDA, e, "memset ws");
@@ -190,6 +199,10 @@ fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, c
   if (!info.empty() &&
       (e = cudaMemcpyAsync(f->piece_info, info.data(), info.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cleanup(FX_ECUDA, e, "copy info");
+  if (!rootrec.empty() &&
+      (e = cudaMemcpyAsync(f->piece_root, rootrec.data(), rootrec.size() * 4, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+    return cleanup(FX_ECUDA, e, "copy root records");
   if (!rad.empty() &&
       (e = cudaMemcpyAsync(f->piece_rad, rad.data(), rad.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cleanup(FX_ECUDA, e, "copy rad");
@@ -208,6 +221,7 @@ void fiber_free(fx_fibers* f) {
   cudaFree(f->piece_info);
   cudaFree(f->seg_cp);
   cudaFree(f->piece_rad);
+  cudaFree(f->piece_root);
   cudaFree(f->ws);
   cudaFree(f->stage);
   delete f;

@@ -23,6 +23,7 @@ struct fx_fibers {
   int32_t *piece_begin = nullptr;       // n_seg + 1
   int32_t *piece_info = nullptr;        // n_piece: level | off << 4 | unsupported << 31
   float *piece_rad = nullptr;           // n_piece: root conservative radius
+  float4 *piece_root = nullptr;         // n_piece x {p.xyz, root radius}, {d.xyz, 0}
   float4 *seg_cp = nullptr;             // n_seg x 4 control points (backward, polish)
   uint32_t *ws = nullptr;               // FX_WS_WORDS words + 8 uint64 counters
   fx_launch launch{128, 0, 32, FX_VARIANT_LANE};  // blocks_per_sm 0: as many as fit
@@ -40,6 +41,7 @@ struct TraceArgs {
   const int32_t *piece_begin;
   const int32_t *piece_info;
   const float *piece_rad;
+  const float4 *piece_root;
   const float4 *rays;
   const int32_t *row_ptr;
   const int32_t *seg_idx;

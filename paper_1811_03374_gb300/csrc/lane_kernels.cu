@@ -10,15 +10,15 @@
 // traversal state is the paper's bit string, start and size in registers
 // (Sec. 3.3).
 //
-// Latency of the per-candidate gathers is taken off the critical path by a
-// per-lane software pipeline: the piece (64 B) and its root radius of the next
-// candidate are copied into the lane's shared-memory slot with cp.async while
-// the current one is traversed, and segment ids are loaded two candidates
-// ahead.  Most candidates miss their root cylinder, so the root test needs
-// only p and d in the ray frame and the piece's precomputed root radius (a
-// rigid motion does not change it); t0, t1 are rotated, the root node saved
-// for backtracking (in shared memory) and the slab (two plane divisions)
-// formed only once that cylinder is hit.
+// Most candidates miss their root cylinder.  The root test needs only p and d
+// of the piece and its conservative radius, which a rigid motion leaves
+// unchanged and the upload precomputes; these 32-byte root records stream
+// through a 4-slot ring per lane in shared memory, copied with cp.async three
+// candidates ahead of use (segment ids five ahead), so the gathers overlap the
+// tests of the preceding candidates.  Only when a root cylinder is hit is the
+// full 64-byte piece read and rotated into the ray frame; after a backtrack
+// the root node is rebuilt from it the same way.  The slab of a node (two
+// plane divisions) is formed only once its cylinder is hit.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -30,6 +30,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLaneBlock = 128;
+constexpr int kRing = 4;  // slots per lane: the current candidate and three ahead
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -38,22 +39,25 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(saddr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void wait_ring() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+}
 __device__ __forceinline__ void wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-struct Lite {  // traversal state kept in registers (the root node is in shared memory)
+struct Lite {  // traversal state kept in registers
   Node c;
   float tmin, tmax;
   uint32_t bits, start, size, min_size;
-  int32_t info, iters;
-  float root_r;   // precomputed radius of the root cylinder
-  bool slab_ok;   // tmin / tmax hold the current node's slab
-  bool at_root;   // t0, t1 not yet rotated (still in the lane's slot)
+  int32_t info, iters, piece;
+  float root_r;  // precomputed radius of the root cylinder
+  bool slab_ok;  // tmin / tmax hold the current node's slab
+  bool at_root;  // only p, d of the root are in the ray frame so far
 };
 
-template <bool FAST>
-__device__ __forceinline__ void to_local(const float4& p, const float4& d, const float4& t0,
-                                         const float4& t1, const RayFrame& r, Node& n) {
+__device__ __forceinline__ void to_local(const float4* __restrict__ piece, int32_t k, const RayFrame& r,
+                                         Node& n) {
+  const float4 p = __ldg(piece + 4 * (int64_t)k), d = __ldg(piece + 4 * (int64_t)k + 1);
+  const float4 t0 = __ldg(piece + 4 * (int64_t)k + 2), t1 = __ldg(piece + 4 * (int64_t)k + 3);
   n.p = rotate(r, p.x - r.o.x, p.y - r.o.y, p.z - r.o.z, p.w);
   n.d = rotate(r, d.x, d.y, d.z, d.w);
   n.t0 = rotate(r, t0.x, t0.y, t0.z, t0.w);
@@ -61,10 +65,8 @@ __device__ __forceinline__ void to_local(const float4& p, const float4& d, const
 }
 
 template <bool FAST, bool PAIRS, bool COUNT, bool IDENTITY>
-__global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int check) {
-  __shared__ __align__(16) float4 s_slot[2][4][kLaneBlock];  // [parity][component][lane]
-  __shared__ float s_rad[2][kLaneBlock];
-  __shared__ __align__(16) float4 s_root[4][kLaneBlock];
+__global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int check) {
+  __shared__ __align__(16) float4 s_rec[kRing][2][kLaneBlock];  // [slot][p|d][lane]
   const int tid = threadIdx.x, lane = tid & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -73,8 +75,8 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
 
   int64_t ray = -1;
   int32_t cand = 0, cend = 0, crow = 0;
-  int32_t s_cur = -1, s_n1 = -1, s_n2 = -1;  // segment ids of cand, cand + 1, cand + 2
-  int32_t pc = 0, pend = 0;                   // remaining pieces of a pre-split segment
+  int32_t s_cur = -1, q1 = -1, q2 = -1, q3 = -1, q4 = -1, q5 = -1;  // ids of cand, cand + 1..5
+  int32_t pc = 0, pend = 0;  // remaining pieces of a pre-split segment
   RayFrame rf;
   float ray_tmax = 0.0f, best_t = 0.0f, best_u = -1.0f;
   int32_t best_seg = -1, best_leaf = -1;
@@ -84,26 +86,17 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
   Lite st;
   uint32_t n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
 
-  // Loaded ids are checked only where they are used (one and two candidates
-  // later), so the loads stay off the critical path.
+  // Ids are checked where they are used, so their loads stay off the
+  // critical path.
   auto seg_at = [&](int32_t j) -> int32_t { return j < cend ? __ldg(a.seg_idx + j) : -1; };
-  auto valid = [&](int32_t s) -> bool {
-    if (s < 0) return false;
-    if (check && s >= a.n_seg) return false;
-    return true;
-  };
-  auto prefetch = [&](int32_t s, int parity) {
+  auto valid = [&](int32_t s) -> bool { return s >= 0 && (!check || s < a.n_seg); };
+  auto prefetch = [&](int32_t s, int32_t pos) {
     if (IDENTITY && valid(s)) {
-      const float4* src = a.piece + 4 * (int64_t)s;
-      cp16(&s_slot[parity][0][tid], src);
-      cp16(&s_slot[parity][1][tid], src + 1);
-      cp16(&s_slot[parity][2][tid], src + 2);
-      cp16(&s_slot[parity][3][tid], src + 3);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr(&s_rad[parity][tid])),
-                   "l"(a.piece_rad + s)
-                   : "memory");
+      const int slot = pos & (kRing - 1);
+      cp16(&s_rec[slot][0][tid], a.piece_root + 2 * (int64_t)s);
+      cp16(&s_rec[slot][1][tid], a.piece_root + 2 * (int64_t)s + 1);
     }
-    commit();
+    commit();  // one group per candidate, empty or not
   };
   auto init_state = [&](int32_t info) {
     st.bits = 0;
@@ -117,24 +110,22 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
     active = true;
     if (COUNT) ++n_tests;
   };
-  // Piece k from global memory, fully rotated (pre-split segments).
+  // Piece k read from global memory and rotated in full (pre-split segments).
   auto begin_piece_k = [&](int32_t k) {
-    to_local<FAST>(__ldg(a.piece + 4 * (int64_t)k), __ldg(a.piece + 4 * (int64_t)k + 1),
-                   __ldg(a.piece + 4 * (int64_t)k + 2), __ldg(a.piece + 4 * (int64_t)k + 3), rf, st.c);
-    s_root[0][tid] = st.c.p;
-    s_root[1][tid] = st.c.d;
-    s_root[2][tid] = st.c.t0;
-    s_root[3][tid] = st.c.t1;
+    to_local(a.piece, k, rf, st.c);
+    st.piece = k;
     st.root_r = __ldg(a.piece_rad + k);
     st.at_root = false;
     init_state(__ldg(a.piece_info + k));
   };
-  // Piece of the current candidate from the lane's slot: only p and d rotated.
-  auto begin_slot = [&](int par) {
-    const float4 p = s_slot[par][0][tid], d = s_slot[par][1][tid];
-    st.c.p = rotate(rf, p.x - rf.o.x, p.y - rf.o.y, p.z - rf.o.z, p.w);
-    st.c.d = rotate(rf, d.x, d.y, d.z, d.w);
-    st.root_r = s_rad[par][tid];
+  // The current candidate's root record from its slot: p and d rotated.
+  auto begin_slot = [&](int32_t pos) {
+    const int slot = pos & (kRing - 1);
+    const float4 p = s_rec[slot][0][tid], d = s_rec[slot][1][tid];
+    st.c.p = rotate(rf, p.x - rf.o.x, p.y - rf.o.y, p.z - rf.o.z, 0.0f);
+    st.c.d = rotate(rf, d.x, d.y, d.z, 0.0f);
+    st.root_r = p.w;
+    st.piece = s_cur;
     st.at_root = true;
     init_state(0);
   };
@@ -162,9 +153,12 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
         ray = -1;
         return;
       }
-      s_cur = s_n1;
-      s_n1 = s_n2;
-      s_n2 = seg_at(cand + 2);
+      s_cur = q1;
+      q1 = q2;
+      q2 = q3;
+      q3 = q4;
+      q4 = q5;
+      q5 = seg_at(cand + 5);
       if (PAIRS) {
         cand_t = ray_tmax;
         cand_u = -1.0f;
@@ -175,10 +169,10 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
         s_cur = -1;
       }
       if (IDENTITY) {
-        prefetch(s_n1, (cand + 1) & 1);  // one group per candidate
-        wait_all_but_one();              // this candidate's group has landed
+        prefetch(q3, cand + 3);
+        wait_ring();  // this candidate's group has landed
         if (s_cur < 0) continue;
-        begin_slot(cand & 1);
+        begin_slot(cand);
         return;
       } else {
         if (s_cur < 0) continue;
@@ -233,9 +227,16 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
           best_leaf = -1;
           cand = crow - 1;
           pc = pend = 0;
-          s_n1 = seg_at(crow);
-          s_n2 = seg_at(crow + 1);
-          if (IDENTITY) prefetch(s_n1, crow & 1);
+          q1 = seg_at(crow);
+          q2 = seg_at(crow + 1);
+          q3 = seg_at(crow + 2);
+          q4 = seg_at(crow + 3);
+          q5 = seg_at(crow + 4);
+          if (IDENTITY) {
+            prefetch(q1, crow);
+            prefetch(q2, crow + 1);
+            prefetch(q3, crow + 2);
+          }
           next_candidate();
         }
       }
@@ -250,15 +251,8 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
       float c0 = 0.0f, c1 = 0.0f;
       bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1);
       if (over && st.at_root) {
-        // the root cylinder is hit: rotate the tangents and keep the root node
-        const int par = cand & 1;
-        const float4 t0 = s_slot[par][2][tid], t1 = s_slot[par][3][tid];
-        st.c.t0 = rotate(rf, t0.x, t0.y, t0.z, t0.w);
-        st.c.t1 = rotate(rf, t1.x, t1.y, t1.z, t1.w);
-        s_root[0][tid] = st.c.p;
-        s_root[1][tid] = st.c.d;
-        s_root[2][tid] = st.c.t0;
-        s_root[3][tid] = st.c.t1;
+        // the root cylinder is hit: the whole piece in the ray frame
+        to_local(a.piece, st.piece, rf, st.c);
         st.at_root = false;
       }
       if (over && !st.slab_ok) {
@@ -299,10 +293,7 @@ __global__ void __launch_bounds__(kLaneBlock, 7) k_lane(const TraceArgs a, int c
       } else {
         jump_up(st.bits, st.start, st.size);
         Node R;
-        R.p = s_root[0][tid];
-        R.d = s_root[1][tid];
-        R.t0 = s_root[2][tid];
-        R.t1 = s_root[3][tid];
+        to_local(a.piece, st.piece, rf, R);  // the root node, rebuilt
         recompute(R, st.start, st.size, st.c);
         st.tmax = pair_tmax;
         st.slab_ok = false;
