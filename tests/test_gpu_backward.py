@@ -23,6 +23,7 @@ def _cuda():
 
 
 GRAZING = 0.05  # |<x - c(u), w>| < GRAZING r(u): the system is near singular
+RIM = 1e-3      # lateral u within RIM of an end: next to the rim of the end disk
 
 
 def _oracle_grad(case, weights, depth):
@@ -30,8 +31,10 @@ def _oracle_grad(case, weights, depth):
     lateral if Newton refinement on the limit surface stays in u in [0, 1],
     otherwise an end-disk hit at the nearer end (t from the disk's plane),
     the rule the adjoint kernel applies.  Grazing lateral hits (incidence
-    cosine below GRAZING) are left out of the check and get zero weight on
-    both sides."""
+    cosine below GRAZING) and hits next to the rim between the lateral
+    surface and an end disk (refined u within RIM of 0 or 1, where dt/dtheta
+    jumps and FP32 and FP64 may classify the hit differently) are left out of
+    the check and get zero weight on both sides."""
     ref = O.closest(case, depth)
     g = np.zeros((case["cps"].shape[0], 4, 4))
     used = np.zeros(len(weights), dtype=bool)
@@ -42,6 +45,8 @@ def _oracle_grad(case, weights, depth):
         w = r7[3:6] / np.linalg.norm(r7[3:6])
         cp = case["cps"][s].astype(np.float64)
         tt, uu = O.refine_hit(r7, cp, ref["t"][i], u)
+        if -RIM < uu < RIM or 1 - RIM < uu < 1 + RIM:
+            continue
         if 0.0 <= uu <= 1.0:
             c = I.bezier(cp[None], np.array([uu]))[0]
             x = r7[:3] + tt * w
