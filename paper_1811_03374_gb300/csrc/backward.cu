@@ -10,11 +10,13 @@
 //   J = [[<w, c'>, <x - c, c''> - |c'|^2], [2 <x - c, w>, -2 <x - c, c'> - 2 r r']],
 //   dG1/dp_k = -B_k c' + B_k' (x - c),  dG2/dp_k = -2 B_k (x - c),
 //   dG2/dr_k = -2 r B_k.
-// A hit is lateral if the refinement converges with u in [0, 1]; otherwise it
-// is an end-disk hit at the nearer end (u fixed at 0 or 1, t from the disk's
-// plane, G1 alone), provided the point lies in the disk.  The forward u
-// cannot tell a lateral hit near an end from the disk in FP32 (u = 1 - 5e-8
-// rounds to 1), so the classification is geometric.
+// Two candidates are formed from the forward (t, u): a lateral hit, refined
+// by Newton steps, valid if u stays in [0, 1]; and a hit of the end disk at
+// the nearer end (u fixed at 0 or 1, t from the disk's plane, G1 alone),
+// valid if the point lies in the disk.  Each must stay close to the forward
+// t; of the valid ones, the one nearer along the ray is the hit.  The forward u cannot tell a lateral
+// hit near an end from the disk in FP32 (u = 1 - 5e-8 rounds to 1), so the
+// classification is geometric.
 // One thread per ray; contributions are added to grad_cps with atomics.
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -72,7 +74,12 @@ __global__ void __launch_bounds__(256)
   const V4 A3{D2.x - 2.f * D1.x + D0.x, D2.y - 2.f * D1.y + D0.y, D2.z - 2.f * D1.z + D0.z,
               D2.w - 2.f * D1.w + D0.w};
   const float t_fwd = tu[r].x, u_fwd = tu[r].y;
-  float t = t_fwd, u = fminf(fmaxf(u_fwd, 1e-6f), 1.0f - 1e-6f);
+  // Newton may leave the forward hit for another root of G (the exit through
+  // the lateral surface of a ray that entered through an end disk): a
+  // candidate counts only within tol of the forward t, a tenth of the largest
+  // control radius, far below the distance between entry and exit except for
+  // grazing rays, whose system is singular anyway.
+  const float tol = 0.1f * fmaxf(fmaxf(P0.w, P1.w), fmaxf(P2.w, P3.w));
 
   V4 c, c1, c2, e;
   float J00 = 0.f, J01 = 0.f, J10 = 0.f, J11 = 0.f;
@@ -96,9 +103,11 @@ __global__ void __launch_bounds__(256)
     J10 = 2.f * d3(e, w);
     J11 = -2.f * d3(e, c1) - 2.f * c.w * c1.w;
   };
+  // candidate 1: the lateral surface, Newton steps from the forward hit
+  float tl = t_fwd, ul = fminf(fmaxf(u_fwd, 1e-6f), 1.0f - 1e-6f);
   bool lateral = true;
   for (int it = 0; it < 5; ++it) {
-    evaluate(u, t);
+    evaluate(ul, tl);
     const float G1 = d3(e, c1), G2 = d3(e, e) - c.w * c.w;
     const float det = J00 * J11 - J01 * J10;
     if (!(fabsf(det) > 0.0f)) {
@@ -106,13 +115,27 @@ __global__ void __launch_bounds__(256)
       break;
     }
     const float id = __frcp_rn(det);
-    t -= (J11 * G1 - J01 * G2) * id;
-    u -= (J00 * G2 - J10 * G1) * id;
+    tl -= (J11 * G1 - J01 * G2) * id;
+    ul -= (J00 * G2 - J10 * G1) * id;
   }
-  lateral = lateral && u >= 0.0f && u <= 1.0f && isfinite(t);
-  float a1 = 0.f, a2 = 0.f;  // dt/dtheta = -(a1 dG1/dtheta + a2 dG2/dtheta)
+  lateral = lateral && ul >= 0.0f && ul <= 1.0f && fabsf(tl - t_fwd) <= tol;
+  // candidate 2: the end disk at the end nearer to the forward u (u fixed,
+  // t where the ray meets the disk's plane, inside the disk)
+  const float ue = u_fwd >= 0.5f ? 1.0f : 0.0f;
+  evaluate(ue, t_fwd);
+  bool disk = fabsf(J00) > 1e-7f * sqrtf(d3(c1, c1));
+  float td = t_fwd;
+  if (disk) {
+    td = t_fwd - d3(e, c1) / J00;  // G1 is linear in t
+    evaluate(ue, td);
+    disk = d3(e, e) <= c.w * c.w * 1.0001f && fabsf(td - t_fwd) <= tol;
+  }
+  // of the valid candidates, the one nearer along the ray is the hit
+  float t, u, a1 = 0.f, a2 = 0.f;  // dt/dtheta = -(a1 dG1/dtheta + a2 dG2/dtheta)
   bool ok;
-  if (lateral) {
+  if (lateral && (!disk || tl <= td)) {
+    t = tl;
+    u = ul;
     evaluate(u, t);
     const float det = J00 * J11 - J01 * J10;
     ok = fabsf(det) > 1e-5f * (fabsf(J00 * J11) + fabsf(J01 * J10));
@@ -122,14 +145,11 @@ __global__ void __launch_bounds__(256)
       a2 = -J01 * id;
     }
   } else {
-    // end disk at the nearer end: t where the ray meets the disk's plane
-    u = u_fwd >= 0.5f ? 1.0f : 0.0f;
-    evaluate(u, t_fwd);
-    ok = fabsf(J00) > 1e-7f * sqrtf(d3(c1, c1));
+    t = td;
+    u = ue;
+    ok = disk;
     if (ok) {
-      t = t_fwd - d3(e, c1) / J00;  // G1 is linear in t
       evaluate(u, t);
-      ok = d3(e, e) <= c.w * c.w * 1.0001f;
       a1 = __frcp_rn(J00);
     }
   }
