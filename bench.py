@@ -60,6 +60,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' x (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, pairs_per_rank, seconds):
+    """Whole-job throughput in G pairs/s: every rank tests its own frame of
+    pairs_per_rank pairs (weak scaling) in at most `seconds`."""
+    return world * pairs_per_rank / seconds / 1e9
+
+
 def emit(obj, args):
     line = json.dumps(obj)
     print(line, flush=True)
@@ -130,9 +146,14 @@ def load_workload(rank=0):
     return case
 
 
+TRAFFIC_KEY = "k_lane_hair"
+
+
 def source_hash():
+    """Hash of the sources of the default kernel (traffic figures taken on
+    another version of it do not apply)."""
     h = hashlib.sha256()
-    for f in ("trace.cuh", "trace_kernels.cu"):
+    for f in ("trace.cuh", "lane_kernels.cu"):
         h.update(open(os.path.join(ROOT, "paper_1811_03374_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -251,7 +272,7 @@ def main():
     depth = args.depth if args.depth is not None else cfg["depth"]
     fast = cfg["fast"] if args.fast is None else bool(args.fast)
     flags = (F.FX_FAST_MATH if fast else 0) | (F.FX_KERNEL_NAIVE if args.kernel == "naive" else 0)
-    fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"])
+    fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"], cfg.get("variant", 0))
 
     tu = torch.empty((n_ray, 2), dtype=torch.float32, device=dev)
     seg = torch.empty(n_ray, dtype=torch.int32, device=dev)
@@ -308,13 +329,10 @@ def main():
     wall = time.perf_counter() - wall0
     clk = clocks.stop() if clocks else None
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_step = float(np.mean(ms))
+    ms_step = max_over_ranks(float(np.mean(ms)), dist, dev)
     if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
-    value = world * n_pair / (ms_step * 1e-3) / 1e9
+    value = job_value(world, n_pair, ms_step * 1e-3)
 
     # ---- end to end through the host-buffer entry (pinned buffers)
     e2e = None
@@ -333,12 +351,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             F.intersect_closest_host(fib, h_rays, h_rp, h_si, depth, flags, out=h_out, stream=stream)
-        dt = (time.perf_counter() - t0) / n_e2e
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * n_pair / dt / 1e9, "unit": UNIT,
+        dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, dist, dev)
+        e2e = {"value": job_value(world, n_pair, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(h_rays.numel() * 4 + h_rp.numel() * 4 + h_si.numel() * 4),
                "d2h_bytes_per_step": int(n_ray * 16), "ms_per_step": dt * 1e3, "steps": n_e2e}
 
@@ -351,7 +365,7 @@ def main():
     sm = info["sm_count"]
     peak = FL.fp32_peak_tflops(sm, 2070.0)
     achieved = work / (ms_step * 1e-3) / 1e12
-    traffic = profiled_traffic("k_persistent_hair")
+    traffic = profiled_traffic(TRAFFIC_KEY)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)" % sm,
@@ -362,7 +376,7 @@ def main():
         roofline["frac_at_sampled_clock"] = achieved / FL.fp32_peak_tflops(sm, clk["sm_mhz"])
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+    if not args.no_cpu_baseline and world == 1:  # rank 0 at N = 1 only
         r = oracle_rate(case, depth, args.cpu_seconds)
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": "%d seeded rays (%.2f%% of the frame) with their %d candidate pairs, "

@@ -7,8 +7,9 @@ Two decisions:
   at the hit for at least 99.9 % of the depth-22 hits.  The method converges
   to its limit surface as the depth grows (Sec. 3.2); d* is where further
   subdivision no longer changes the result at that tolerance.
-* launch shape: threads per block, blocks per SM and the warp's ray chunk,
-  chosen by timing every candidate on the workload with CUDA events.
+* launch shape: the kernel variant (lane- or warp-per-ray), CTAs per SM and
+  the warp's ray chunk, chosen by timing every candidate on the workload with
+  CUDA events.  (The lane kernel's CTA is fixed at 128 threads.)
 
 Results are cached per (GPU name, workload signature) in tune_cache.json next
 to this file; a committed entry serves as the default.
@@ -22,9 +23,10 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tune_cache.json")
-DEFAULT = {"depth": 10, "fast": False, "block": 256, "blocks_per_sm": 0, "chunk": 32}
-BLOCKS = (64, 128, 256)
-CHUNKS = (4, 8, 16, 32, 64, 128)
+DEFAULT = {"depth": 10, "fast": False, "block": 128, "blocks_per_sm": 0, "chunk": 32, "variant": 1}
+VARIANTS = (1, 2)          # FX_VARIANT_LANE, FX_VARIANT_WARP
+BLOCKS_PER_SM = (0, 4, 5)  # 0: as many as fit
+CHUNKS = (8, 16, 32, 64)
 
 
 def _key(fib, n_ray, n_pair):
@@ -99,15 +101,16 @@ def time_launch(fib, rays, row_ptr, seg_idx, depth, flags, reps=20):
 def search_launch(fib, rays, row_ptr, seg_idx, depth, flags=0):
     best = None
     table = []
-    for block in BLOCKS:
-        for chunk in CHUNKS:
-            fib.set_launch(block, 0, chunk)
-            ms = time_launch(fib, rays, row_ptr, seg_idx, depth, flags)
-            table.append((block, chunk, ms))
-            if best is None or ms < best[2]:
-                best = (block, chunk, ms)
-    fib.set_launch(best[0], 0, best[1])
-    return {"block": best[0], "blocks_per_sm": 0, "chunk": best[1], "ms": best[2]}, table
+    for variant in VARIANTS:
+        for bps in BLOCKS_PER_SM:
+            for chunk in CHUNKS:
+                fib.set_launch(128, bps, chunk, variant)
+                ms = time_launch(fib, rays, row_ptr, seg_idx, depth, flags)
+                table.append((variant, bps, chunk, ms))
+                if best is None or ms < best[3]:
+                    best = (variant, bps, chunk, ms)
+    fib.set_launch(128, best[1], best[2], best[0])
+    return {"block": 128, "blocks_per_sm": best[1], "chunk": best[2], "variant": best[0], "ms": best[3]}, table
 
 
 def tuned_config(fib, rays, row_ptr, seg_idx, retune=False, cps=None):

@@ -120,14 +120,15 @@ DEPTHS = [2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 18, 20, 22]
 
 @pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
 @pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
-def test_depth_sweep(klass, forced):
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+def test_depth_sweep(klass, forced, flags):
     case = I.sweep_case(klass, 4096, forced_hits=forced)
     pieces = O.presplit(case["cps"])
     fib = F.Fibers(case["cps"])
     worst = 0.0
     for depth in DEPTHS:
         ref = O.closest(case, depth, pieces)
-        tu, seg, leaf, _ = _run_closest(case, depth, 0, fib)
+        tu, seg, leaf, _ = _run_closest(case, depth, flags, fib)
         stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
         _assert_parity(stats, where="%s depth %d" % (klass, depth))
         worst = max(worst, stats["max_rel_t"])
@@ -248,22 +249,27 @@ def test_upload_rejects_bad_fibers():
 
 @pytest.fixture(scope="module")
 def hair():
-    return I.hair_patch()
-
-
-def test_hair_patch_full_size_sampled(hair):
-    # the benchmark's workload and launch: full frame on the GPU, oracle on a
-    # seeded sample of rays that have candidates
-    case = hair
-    depth = 10
-    tu, seg, leaf, st = _run_closest(case, depth)
-    assert st & ~F.FX_DEV_UNSUPPORTED == 0
+    """The full hair-patch frame and the oracle on a seeded sample of 3000
+    rays that have candidates."""
+    case = I.hair_patch()
     counts = np.diff(case["row_ptr"])
     g = np.random.default_rng(5)
     idx = np.sort(g.choice(np.nonzero(counts > 0)[0], 3000, replace=False))
     sub = I.subsample_rays(case, idx)
     pieces = O.presplit(case["cps"])
-    ref = O.closest(sub, depth, pieces)
+    ref = O.closest(sub, 10, pieces)
+    return case, idx, sub, pieces, ref
+
+
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+def test_hair_patch_full_size_sampled(hair, flags):
+    # the benchmark's workload and launch: full frame on the GPU, oracle on the
+    # sampled rays
+    case, idx, sub, pieces, ref = hair
+    depth = 10
+    tu, seg, leaf, st = _run_closest(case, depth, flags)
+    assert st & ~F.FX_DEV_UNSUPPORTED == 0
+    counts = np.diff(case["row_ptr"])
     stats = P.compare_closest(sub, depth, tu[idx], seg[idx], ref, pieces, leaf[idx])
     _assert_parity(stats, max_band_frac=0.01, where="hair")
     assert stats["hits"] > 500
