@@ -210,6 +210,35 @@ fx_status fx_counters(fx_fibers *f, void *stream, uint64_t *out5, int32_t reset)
  */
 fx_status fx_stream_status(fx_fibers *f, void *stream, uint32_t *device_flags);
 
+/*
+ * intersect_closest_noalloc -- intersect_closest, with the one-thread-per-pair
+ * kernel, for callers that must not allocate device memory while they run:
+ * a renderer whose device memory is handed out up front by another
+ * allocator, or a real-time loop that cannot afford the implicit
+ * synchronisation of cudaMalloc / cudaFree.  (The paper has no counterpart;
+ * this is a property of the library, not of the method.)
+ *
+ * intersect_closest allocates the naive kernel's scratch, one 64-bit key per
+ * ray, on each call.  This entry point allocates nothing: the keys live in a
+ * fixed device array of FX_NOALLOC_MAX_RAYS entries (8 MiB) that every GPU
+ * loading the library holds until the process exits.  The caller passes the
+ * handle, inputs and outputs exactly as for intersect_closest; n_ray above
+ * FX_NOALLOC_MAX_RAYS is refused with FX_EINVAL.  Results equal
+ * intersect_closest with FX_KERNEL_NAIVE and the same flags (FX_FAST_MATH,
+ * FX_COUNT, FX_CHECK_INDEX; FX_POLISH_FP64 needs a non-null leaf).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array: each clears the
+ * keys it uses before its kernels run, and calls that overlap on the GPU
+ * (unordered streams) race on it.
+ */
+#define FX_NOALLOC_MAX_RAYS (1 << 20)
+fx_status intersect_closest_noalloc(const fx_fibers *f, const float *rays, int64_t n_ray,
+                                    const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
+                                    int32_t depth, uint32_t flags, float *tu, int32_t *seg,
+                                    int32_t *leaf, void *stream);
+
 /* Text of the last error on this thread ("" if none). */
 const char *fx_last_error(void);
 

@@ -107,6 +107,10 @@ bool device_is_sm103(int dev, int* sm_count) {
 
 }  // namespace
 
+namespace fx {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace fx
+
 extern "C" {
 
 const char* fx_last_error(void) { return g_err.c_str(); }

@@ -2,6 +2,8 @@
 // part of the public C ABI).
 #pragma once
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 #include "../../include/fiberx.h"
@@ -71,6 +73,9 @@ cudaError_t launch_lane_ray(const TraceArgs &a, bool pairs, uint32_t flags, int 
 // warp_kernels.cu
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
                             int sm_count, cudaStream_t s);
+
+// fiberx_api.cu: text returned by fx_last_error() on this thread
+void set_last_error(const std::string &msg);
 
 // backward.cu
 cudaError_t launch_backward(const float4 *seg_cp, int64_t n_seg, const float4 *rays, int64_t n_ray,

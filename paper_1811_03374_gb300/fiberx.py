@@ -36,8 +36,9 @@ FX_VARIANT_WARP = 2
 
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
-           "intersect_backward", "intersect_closest_host", "fx_set_launch", "fx_get_launch",
-           "fx_counters", "fx_stream_status", "fx_last_error", "fx_version"]
+           "intersect_backward", "intersect_closest_host", "intersect_closest_noalloc", "fx_set_launch",
+           "fx_get_launch", "fx_counters", "fx_stream_status", "fx_last_error", "fx_version"]
+NOALLOC_MAX_RAYS = 1 << 20
 
 
 class FiberxError(RuntimeError):
@@ -92,6 +93,8 @@ def lib():
             L.intersect_backward.restype = i32
             L.intersect_closest_host.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
             L.intersect_closest_host.restype = i32
+            L.intersect_closest_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
+            L.intersect_closest_noalloc.restype = i32
             L.fx_set_launch.argtypes = [vp, ctypes.POINTER(Launch)]
             L.fx_set_launch.restype = i32
             L.fx_get_launch.argtypes = [vp, ctypes.POINTER(Launch)]
@@ -224,6 +227,28 @@ def intersect_closest(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True,
         tu, seg, lf = out
     _check(lib().intersect_closest(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx), n_pair,
                                    int(depth), int(flags), _ptr(tu), _ptr(seg), _ptr(lf), _stream(stream)))
+    return tu, seg, lf
+
+
+def intersect_closest_noalloc(fibers, rays, row_ptr, seg_idx, depth, flags=0, out=None, stream=None):
+    """intersect_closest on the one-thread-per-pair kernel without any device
+    allocation inside the library: its per-ray scratch is a fixed 8 MiB device
+    array shared by all calls (at most NOALLOC_MAX_RAYS rays; calls that
+    overlap on the GPU race on it).  For callers that cannot allocate device
+    memory while they run; pass preallocated ``out = (tu, seg, leaf)`` and
+    device inputs so that this wrapper allocates nothing either."""
+    import torch
+    rays, row_ptr, seg_idx = _inputs(fibers, rays, row_ptr, seg_idx)
+    n_ray, n_pair = rays.shape[0], seg_idx.numel()
+    if out is None:
+        tu = torch.empty((n_ray, 2), dtype=torch.float32, device=fibers.device)
+        seg = torch.empty(n_ray, dtype=torch.int32, device=fibers.device)
+        lf = torch.empty(n_ray, dtype=torch.int32, device=fibers.device)
+    else:
+        tu, seg, lf = out
+    _check(lib().intersect_closest_noalloc(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx),
+                                           n_pair, int(depth), int(flags), _ptr(tu), _ptr(seg), _ptr(lf),
+                                           _stream(stream)))
     return tu, seg, lf
 
 
