@@ -80,13 +80,19 @@ typedef struct {
 } fx_fibers_info;
 
 /* Persistent kernel variants (fx_launch.variant). */
-#define FX_VARIANT_AUTO 0 /* the library's choice (lane per ray) */
-#define FX_VARIANT_LANE 1 /* each lane owns a ray and walks its candidates front to back */
-#define FX_VARIANT_WARP 2 /* a warp owns a ray; its candidates are staged in shared memory */
+#define FX_VARIANT_AUTO 0   /* the library's choice (LANE) */
+#define FX_VARIANT_LANE 1   /* each lane owns a ray and walks its candidates front to back */
+#define FX_VARIANT_WARP 2   /* a warp owns a ray; its candidates are staged in shared memory */
+#define FX_VARIANT_FILTER 3 /* two phases: the root test of every pair, one lane per pair, then
+                               LANE's traversal of the passing candidates of the rays that have
+                               any.  Same results and counters as LANE.  intersect_closest on
+                               handles whose segments are single level-0 pieces (none pre-split
+                               or unsupported) only; elsewhere LANE runs.  Its work lists
+                               (8 B per pair, 8 B per ray) come from the handle's memory pool. */
 
 /* Launch configuration of the persistent kernels (fx_set_launch). */
 typedef struct {
-    int32_t block;         /* reserved: 64, 128 or 256 (both variants run 128-thread blocks) */
+    int32_t block;         /* reserved: 64, 128 or 256 (the variants fix their own block sizes) */
     int32_t blocks_per_sm; /* blocks per SM the grid is sized for (1..16; 0 = as many as fit) */
     int32_t chunk;         /* lane-per-ray: rays a warp takes from the queue at a time (1..1024) */
     int32_t variant;       /* FX_VARIANT_* */
@@ -139,6 +145,9 @@ fx_status fiber_info(const fx_fibers *f, fx_fibers_info *out);
  * t = +inf, u = -1), seg (int32, -1 on miss), leaf (nullable; int32 start of
  * the hit leaf in units of 2^-23 of the segment; -1 on miss).
  * flags: FX_KERNEL_*, FX_FAST_MATH, FX_POLISH_FP64, FX_COUNT, FX_CHECK_INDEX.
+ * Scratch (FX_VARIANT_FILTER's work lists, the naive kernel's per-ray keys,
+ * a leaf buffer for the polish) is allocated stream-ordered from a memory
+ * pool owned by the handle, which keeps freed memory for the next call.
  * Errors: FX_EINVAL, FX_EDEPTH, FX_ECUDA.
  */
 fx_status intersect_closest(const fx_fibers *f, const float *rays, int64_t n_ray,

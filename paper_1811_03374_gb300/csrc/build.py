@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libfiberx.so")
-SOURCES = ["lane_kernels.cu", "trace_kernels.cu", "warp_kernels.cu", "backward.cu", "fiberx_api.cu",
+SOURCES = ["filter_kernels.cu", "lane_kernels.cu", "trace_kernels.cu", "warp_kernels.cu", "backward.cu", "fiberx_api.cu",
            "noalloc.cu", "presplit.cpp"]
 HEADERS = ["trace.cuh", "internal.h", "presplit.h", os.path.join(ROOT, "include", "fiberx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,8 +36,12 @@ def stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
-    out_dir = os.path.join(HERE, "_build")
+def build(verbose: bool = False, extra: list[str] | None = None, out: str | None = None,
+          obj_dir: str | None = None) -> str:
+    """Compiles and links the library; `extra` nvcc flags, `out` / `obj_dir`
+    redirect the result (default: the in-tree libfiberx.so)."""
+    lib = out or LIB
+    out_dir = obj_dir or os.path.join(HERE, "_build")
     os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -55,17 +59,17 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
 
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         results = list(ex.map(one, SOURCES))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         for _, log in results:
             if log:
                 print(log)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

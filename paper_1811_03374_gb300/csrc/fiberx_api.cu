@@ -79,7 +79,7 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
   if (flags & FX_KERNEL_NAIVE) {
     unsigned long long* scratch = nullptr;
     if (!pairs) {
-      FX_CUDA(cudaMallocAsync((void**)&scratch, sizeof(unsigned long long) * a.n_ray, s));
+      FX_CUDA(cudaMallocFromPoolAsync((void**)&scratch, sizeof(unsigned long long) * a.n_ray, f->pool, s));
       FX_CUDA(cudaMemsetAsync(scratch, 0xff, sizeof(unsigned long long) * a.n_ray, s));
     }
     a.scratch = scratch;
@@ -89,7 +89,29 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
     return FX_OK;
   }
   FX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s));
-  const int variant = f->launch.variant == FX_VARIANT_AUTO ? FX_VARIANT_LANE : f->launch.variant;
+  int variant = f->launch.variant;
+  if (variant == FX_VARIANT_AUTO) variant = FX_VARIANT_LANE;
+  // the two-phase path covers closest hits on handles of single level-0 pieces
+  if (variant == FX_VARIANT_FILTER && (pairs || !f->identity)) variant = FX_VARIANT_LANE;
+  if (variant == FX_VARIANT_FILTER) {
+    int2* pass = nullptr;
+    int32_t* ibuf = nullptr;
+    FX_CUDA(cudaMallocFromPoolAsync((void**)&pass, sizeof(int2) * (size_t)std::max<int64_t>(1, a.n_pair),
+                                    f->pool, s));
+    cudaError_t e = cudaMallocFromPoolAsync((void**)&ibuf, sizeof(int32_t) * (size_t)(2 * a.n_ray + 4), f->pool, s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(pass, s);
+      return cuda_fail(e, "cudaMallocFromPoolAsync filter lists");
+    }
+    fx::FilterArgs o{pass, ibuf, ibuf + a.n_ray, reinterpret_cast<uint32_t*>(ibuf + 2 * a.n_ray),
+                     reinterpret_cast<uint32_t*>(ibuf + 2 * a.n_ray + 1)};
+    e = cudaMemsetAsync(o.n_active, 0, 2 * sizeof(uint32_t), s);  // n_active, group_queue
+    if (e == cudaSuccess) e = fx::launch_filter(a, o, flags, f->launch.blocks_per_sm, f->sm_count, s);
+    cudaFreeAsync(ibuf, s);
+    cudaFreeAsync(pass, s);
+    if (e != cudaSuccess) return cuda_fail(e, "filter kernels");
+    return FX_OK;
+  }
   if (variant == FX_VARIANT_WARP) {
     FX_CUDA(fx::launch_warp_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
   } else {
@@ -171,11 +193,11 @@ fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, c
       rootrec[8 * k + 4 + a] = pieces[k].pdt[4 + a];  // d
     }
     rootrec[8 * k + 3] = pieces[k].root_radius;
-    rootrec[8 * k + 7] = 0.0f;
+    rootrec[8 * k + 7] = pieces[k].bound_radius;
     info[k] = pieces[k].level | (pieces[k].off << 4) | (pieces[k].unsupported ? (int32_t)0x80000000 : 0);
     f->max_level = std::max(f->max_level, pieces[k].level);
     if (pieces[k].unsupported) f->n_unsupported++;
-    if (pieces[k].level != 0) f->identity = false;
+    if (pieces[k].level != 0 || pieces[k].unsupported) f->identity = false;
   }
   for (int64_t i = 0; i < n_seg; ++i)
     if (begin[i + 1] - begin[i] > 1) f->n_presplit++;
@@ -192,6 +214,16 @@ fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, c
   if ((e = cudaMalloc((void**)&f->seg_cp, ns * 64)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc seg_cp");
   if ((e = cudaMalloc((void**)&f->piece_rad, np * 4)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc rad");
   if ((e = cudaMalloc((void**)&f->piece_root, np * 32)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc root");
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if ((e = cudaMemPoolCreate(&f->pool, &props)) != cudaSuccess) return cleanup(FX_ECUDA, e, "cudaMemPoolCreate");
+    uint64_t keep = UINT64_MAX;
+    if ((e = cudaMemPoolSetAttribute(f->pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+      return cleanup(FX_ECUDA, e, "cudaMemPoolSetAttribute");
+  }
   const size_t ws_bytes = FX_WS_WORDS * 4 + 8 * 8;
   if ((e = cudaMalloc((void**)&f->ws, ws_bytes)) != cudaSuccess) return cleanup(FX_ENOMEM, e, "cudaMalloc ws");
   if ((e = cudaMemsetAsync(f->ws, 0, ws_bytes, s)) != cudaSuccess) return cleanup(FX_ECUDA, e, "memset ws");
@@ -228,6 +260,7 @@ void fiber_free(fx_fibers* f) {
   cudaFree(f->piece_root);
   cudaFree(f->ws);
   cudaFree(f->stage);
+  if (f->pool) cudaMemPoolDestroy(f->pool);  // released once its last allocation is freed
   delete f;
 }
 
@@ -248,7 +281,7 @@ fx_status fx_set_launch(fx_fibers* f, const fx_launch* cfg) {
   if (!(b == 64 || b == 128 || b == 256)) return fail(FX_EINVAL, "block must be 64, 128 or 256");
   if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 16) return fail(FX_EINVAL, "blocks_per_sm outside [0, 16]");
   if (cfg->chunk < 1 || cfg->chunk > 1024) return fail(FX_EINVAL, "chunk outside [1, 1024]");
-  if (cfg->variant < FX_VARIANT_AUTO || cfg->variant > FX_VARIANT_WARP) return fail(FX_EINVAL, "unknown variant");
+  if (cfg->variant < FX_VARIANT_AUTO || cfg->variant > FX_VARIANT_FILTER) return fail(FX_EINVAL, "unknown variant");
   f->launch = *cfg;
   return FX_OK;
 }
@@ -272,7 +305,7 @@ fx_status intersect_closest(const fx_fibers* f, const float* rays, int64_t n_ray
   a.leaf = leaf;
   int32_t* tmp_leaf = nullptr;
   if ((flags & FX_POLISH_FP64) && !leaf && n_ray > 0) {
-    FX_CUDA(cudaMallocAsync((void**)&tmp_leaf, sizeof(int32_t) * n_ray, s));
+    FX_CUDA(cudaMallocFromPoolAsync((void**)&tmp_leaf, sizeof(int32_t) * n_ray, f->pool, s));
     a.leaf = tmp_leaf;
   }
   st = run_forward(f, a, false, flags, s);

@@ -20,7 +20,7 @@ struct fx_fibers {
   int sm_count = 0;
   int64_t n_seg = 0, n_piece = 0, n_presplit = 0, n_unsupported = 0;
   int32_t max_level = 0;
-  bool identity = true;                 // one level-0 piece per segment
+  bool identity = true;                 // one level-0 piece per segment, none unsupported
   float4 *piece = nullptr;              // n_piece x {p, d, t0, t1} world space
   int32_t *piece_begin = nullptr;       // n_seg + 1
   int32_t *piece_info = nullptr;        // n_piece: level | off << 4 | unsupported << 31
@@ -29,6 +29,9 @@ struct fx_fibers {
   float4 *seg_cp = nullptr;             // n_seg x 4 control points (backward, polish)
   uint32_t *ws = nullptr;               // FX_WS_WORDS words + 8 uint64 counters
   fx_launch launch{128, 0, 32, FX_VARIANT_LANE};  // blocks_per_sm 0: as many as fit
+  // stream-ordered scratch of the intersect calls; keeps its memory between
+  // calls (release threshold: never), so repeated calls do not remap it
+  cudaMemPool_t pool = nullptr;
   // host-buffer entry staging (grow-only)
   void *stage = nullptr;
   size_t stage_bytes = 0;
@@ -62,6 +65,15 @@ struct TraceArgs {
   unsigned long long *scratch;   // naive kernel: per-ray packed (t, pair) keys
 };
 
+// Work lists of the two-phase path (filter_kernels.cu), allocated per call.
+struct FilterArgs {
+  int2 *pass;          // n_pair, CSR aligned: {segment, entry bound as float bits} of passing pairs
+  int32_t *pass_cnt;   // n_ray: passing pairs per ray
+  int32_t *active;     // n_ray: rays with at least one passing pair (first *n_active entries)
+  uint32_t *n_active;  // 1, zeroed before the filter runs
+  uint32_t *group_queue;  // 1, zeroed before the filter runs: next group of 32 rays
+};
+
 // Launchers (trace_kernels.cu).  flags: FX_* bits of the public header.
 cudaError_t launch_naive(const TraceArgs &a, bool pairs, uint32_t flags, cudaStream_t s);
 cudaError_t launch_polish(const TraceArgs &a, const float4 *seg_cp, cudaStream_t s);
@@ -69,6 +81,11 @@ cudaError_t launch_polish(const TraceArgs &a, const float4 *seg_cp, cudaStream_t
 // lane_kernels.cu
 cudaError_t launch_lane_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
                             int sm_count, cudaStream_t s);
+
+// filter_kernels.cu: root filter, then traversal of the active rays (closest
+// hit, handles with single level-0 pieces only)
+cudaError_t launch_filter(const TraceArgs &a, const FilterArgs &o, uint32_t flags, int blocks_per_sm_cap,
+                          int sm_count, cudaStream_t s);
 
 // warp_kernels.cu
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,

@@ -30,7 +30,20 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLaneBlock = 128;
-constexpr int kRing = 4;  // slots per lane: the current candidate and three ahead
+#ifndef FX_LANE_RING
+#define FX_LANE_RING 4
+#endif
+#ifndef FX_LANE_SKIP
+#define FX_LANE_SKIP 1
+#endif
+constexpr int kRing = FX_LANE_RING;  // slots per lane (4 or 8)
+// root records are copied this many candidates ahead of use; the ids of the
+// next five (ring of 4) or seven (ring of 8) candidates are held in registers
+constexpr int kAhead = kRing == 8 ? 6 : 3;
+static_assert(kRing == 4 || kRing == 8, "ring of 4 or 8 slots");
+constexpr int kSkipCap = FX_LANE_SKIP;  // candidates a lane may reject by their bound in one step
+// relative slack of the bound test against FP32 rounding of the rotation
+constexpr float kBoundSlack = 1.0f / 262144.0f;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -40,7 +53,7 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void wait_ring() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kAhead) : "memory");
 }
 __device__ __forceinline__ void wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -75,7 +88,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
 
   int64_t ray = -1;
   int32_t cand = 0, cend = 0, crow = 0;
-  int32_t s_cur = -1, q1 = -1, q2 = -1, q3 = -1, q4 = -1, q5 = -1;  // ids of cand, cand + 1..5
+  int32_t s_cur = -1, q1 = -1, q2 = -1, q3 = -1, q4 = -1, q5 = -1, q6 = -1, q7 = -1;  // cand, cand + 1..7
   int32_t pc = 0, pend = 0;  // remaining pieces of a pre-split segment
   RayFrame rf;
   float ray_tmax = 0.0f, best_t = 0.0f, best_u = -1.0f;
@@ -118,16 +131,28 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
     st.at_root = false;
     init_state(__ldg(a.piece_info + k));
   };
-  // The current candidate's root record from its slot: p and d rotated.
-  auto begin_slot = [&](int32_t pos) {
+  // The current candidate's root record from its slot.  The record's d.w is
+  // the radius of a sphere around the chord's midpoint that holds the root
+  // node's capped cylinder (the region its test can accept); if the whole
+  // sphere lies beyond the closest hit so far, the root test cannot pass and
+  // the candidate is rejected from the ray-frame z components alone.
+  // Otherwise p and d are rotated.  Returns false on a rejection.
+  auto begin_slot = [&](int32_t pos) -> bool {
     const int slot = pos & (kRing - 1);
     const float4 p = s_rec[slot][0][tid], d = s_rec[slot][1][tid];
-    st.c.p = rotate(rf, p.x - rf.o.x, p.y - rf.o.y, p.z - rf.o.z, 0.0f);
+    const float px = p.x - rf.o.x, py = p.y - rf.o.y, pz = p.z - rf.o.z;
+    const float zp = fmaf(px, rf.w.x, fmaf(py, rf.w.y, pz * rf.w.z));
+    const float zd = fmaf(d.x, rf.w.x, fmaf(d.y, rf.w.y, d.z * rf.w.z));
+    const float near = fmaf(0.5f, zd, zp) - d.w;
+    const float lim = PAIRS ? cand_t : best_t;
+    if (near - kBoundSlack * (fabsf(zp) + fabsf(zd) + d.w) > lim) return false;
+    st.c.p = rotate(rf, px, py, pz, 0.0f);
     st.c.d = rotate(rf, d.x, d.y, d.z, 0.0f);
     st.root_r = p.w;
     st.piece = s_cur;
     st.at_root = true;
     init_state(0);
+    return true;
   };
   auto finish_candidate = [&]() {
     if (PAIRS) {
@@ -135,8 +160,11 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
       if (a.leaf) a.leaf[cand] = cand_leaf;
     }
   };
-  // Moves to the next candidate of the ray (or finishes the ray).
+  // Moves to the next candidate of the ray (or finishes the ray).  A lane
+  // rejects at most kSkipCap candidates by their bound per step, so that one
+  // lane's long run of rejections does not hold up the rest of its warp.
   auto next_candidate = [&]() {
+    int rejected = 0;
     while (ray >= 0) {
       if (!IDENTITY && pc < pend) {
         begin_piece_k(pc++);
@@ -158,7 +186,14 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
       q2 = q3;
       q3 = q4;
       q4 = q5;
-      q5 = seg_at(cand + 5);
+      if (kRing == 8) {  // ids seven ahead
+        q5 = q6;
+        q6 = q7;
+        q7 = seg_at(cand + 7);
+      } else {  // ids five ahead
+        q5 = seg_at(cand + 5);
+      }
+      const int32_t q_ahead = kAhead == 6 ? q6 : q3;
       if (PAIRS) {
         cand_t = ray_tmax;
         cand_u = -1.0f;
@@ -169,11 +204,13 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
         s_cur = -1;
       }
       if (IDENTITY) {
-        prefetch(q3, cand + 3);
+        prefetch(q_ahead, cand + kAhead);
         wait_ring();  // this candidate's group has landed
         if (s_cur < 0) continue;
-        begin_slot(cand);
-        return;
+        if (begin_slot(cand)) return;
+        if (COUNT) ++n_tests;
+        if (++rejected >= kSkipCap) return;  // the lane idles this step
+        continue;
       } else {
         if (s_cur < 0) continue;
         pc = __ldg(a.piece_begin + s_cur);
@@ -232,17 +269,24 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
           q3 = seg_at(crow + 2);
           q4 = seg_at(crow + 3);
           q5 = seg_at(crow + 4);
+          if (kRing == 8) {
+            q6 = seg_at(crow + 5);
+            q7 = seg_at(crow + 6);
+          }
           if (IDENTITY) {
             prefetch(q1, crow);
             prefetch(q2, crow + 1);
-            prefetch(q3, crow + 2);
+            prefetch(q3, crow + 2);  // kAhead >= 3
+            if (kAhead > 3) prefetch(q4, crow + 3);
+            if (kAhead > 4) prefetch(q5, crow + 4);
+            if (kAhead > 5) prefetch(q6, crow + 5);
           }
           next_candidate();
         }
       }
       pool_next += min((int64_t)__popc(m), avail);
     }
-    if (__all_sync(kFull, !active)) break;
+    if (__all_sync(kFull, !active && ray < 0)) break;
 
     // ---- 2. one node step per active lane ----------------------------------
     if (active) {

@@ -127,6 +127,28 @@ void halve(const Curve& c, Curve& L, Curve& R) {
   }
 }
 
+// Radius of a sphere about the chord midpoint p0 + d/2 that holds the root
+// node's capped cylinder: the points within rc of the chord line between the
+// start plane (through p0, normal t0) and the end plane (through p0 + d,
+// normal t1).  Along the axis a point at distance q <= rc from it reaches at
+// most rc |t_perp| / <d^, t> past an end plane's foot, so the region lies in
+// the capsule a in [-e0, |d| + e1] x radius rc.  An end plane that does not
+// face along the chord leaves the region unbounded: +inf.  Rounded up in
+// FP32 with a relative margin for the kernel's FP32 evaluation.
+float capped_bound(const P4& d, const P4& t0, const P4& t1, double rc) {
+  const double L = std::sqrt(dot(d, d));
+  if (!(L > 0.0)) return INFINITY;
+  const double a0 = dot(d, t0) / L, a1 = dot(d, t1) / L;  // tangent components along the chord
+  if (!(a0 > 0.0) || !(a1 > 0.0)) return INFINITY;
+  const double p0 = std::sqrt(std::max(0.0, dot(t0, t0) - a0 * a0));
+  const double p1 = std::sqrt(std::max(0.0, dot(t1, t1) - a1 * a1));
+  const double e0 = rc * p0 / a0, e1 = rc * p1 / a1;
+  const double h = 0.5 * L + std::max(e0, e1);
+  const double R = std::sqrt(h * h + rc * rc) * (1.0 + 1e-6);
+  const float f = (float)R;
+  return (double)f >= R ? f : std::nextafter(f, INFINITY);
+}
+
 void emit(const Curve& c, int level, int off, bool ok, std::vector<PieceRec>& out) {
   PieceRec p;
   const P4 d = sub(c[3], c[0]), t0 = sub(c[1], c[0]), t1 = sub(c[3], c[2]);
@@ -152,7 +174,9 @@ void emit(const Curve& c, int level, int off, bool ok, std::vector<PieceRec>& ou
   }
   double rmax = 0.0;
   for (const P4& cpk : c) rmax = std::max(rmax, cpk.v[3]);
-  p.root_radius = (float)(std::sqrt(m) + rmax);
+  const double rc = std::sqrt(m) + rmax;
+  p.root_radius = (float)rc;
+  p.bound_radius = capped_bound(d, t0, t1, rc * (1.0 + 1e-6));
   p.level = level;
   p.off = off;
   p.unsupported = !ok;

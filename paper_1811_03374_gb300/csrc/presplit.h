@@ -9,6 +9,8 @@ namespace fx {
 struct PieceRec {
   float pdt[16];  // (p, d, t0, t1) x (x, y, z, r), world space
   float root_radius;  // conservative radius of the piece's bounding cylinder (Sec. 3.3)
+  float bound_radius; // sphere about the chord midpoint holding the root node's capped
+                      // cylinder (+inf when an end plane does not bound it)
   int32_t level;  // pre-split level k (the piece is [off, off + 1] * 2^-k)
   int32_t off;
   bool unsupported;

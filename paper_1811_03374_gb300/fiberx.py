@@ -33,6 +33,7 @@ FX_CHECK_INDEX = 0x10
 FX_VARIANT_AUTO = 0
 FX_VARIANT_LANE = 1
 FX_VARIANT_WARP = 2
+FX_VARIANT_FILTER = 3
 
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
@@ -67,7 +68,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree library, or the build named by FIBERX_LIB (a library built
+    with other compile-time settings, for comparing them)."""
+    return os.environ.get("FIBERX_LIB") or _build.LIB
 
 
 def lib():
@@ -75,9 +78,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            if _build.stale():
+            path = library_path()
+            if path == _build.LIB and _build.stale():
                 _build.build()
-            L = ctypes.CDLL(_build.LIB)
+            L = ctypes.CDLL(path)
             vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
             L.fiber_upload.argtypes = [vp, i64, i32, ctypes.POINTER(UploadOpts), vp, ctypes.POINTER(vp)]
             L.fiber_upload.restype = i32

@@ -3,18 +3,29 @@
 Counts follow the arithmetic of each step as the kernels perform it (an add,
 subtract or multiply is one flop, a fused multiply-add two, a reciprocal,
 division or square root one); comparisons, selects and integer bit-string
-work are not counted.
+work are not counted.  Work that only some events need is not charged (the
+slab and the rotation of t0, t1 that a passing root cylinder needs), so the
+totals are lower bounds.
 
-  per ray      normalise the direction, Duff et al.'s basis          20
-  per test     origin offset + rotation of (p, d, t0, t1), slab      78
-  per node     conservative radius (44) + unit-ray cylinder (24)     68
-  per descent  split terms, plane, child selection                   49
-  per backtrack  power-form recomputation (142) + slab (15)         157
-  per hit      u by projection onto the leaf axis, segment mapping   17
+  per ray          normalise the direction, Duff et al.'s basis          20
+  per candidate    origin offset, ray-frame z of p and d, the bound of
+                   the root node's capped cylinder against t_max          20
+  per root node    x, y of p and d in the ray frame (20) + unit-ray
+                   cylinder with the precomputed root radius (24)         44
+  per deeper node  conservative radius (44) + unit-ray cylinder (24)      68
+  per descent      split terms, plane, child selection                    49
+  per backtrack    power-form recomputation (142) + slab (15)            157
+  per hit          u by projection onto the leaf axis, segment mapping    17
+
+Counters (all variants): tests = candidate pieces examined, nodes = node
+tests including roots, descents, backtracks, hits.  Every deeper node test
+follows a descent or a backtrack, so root node tests = nodes - descents -
+backtracks.
 """
 
 PER_RAY = 20
-PER_TEST = 78
+PER_BOUND = 20
+PER_ROOT = 44
 PER_NODE = 68
 PER_DESCENT = 49
 PER_BACKTRACK = 157
@@ -30,8 +41,10 @@ BYTES_PER_PIECE = 64
 
 def alg_flops(counters, n_ray_with_candidates):
     c = counters
-    return (PER_RAY * n_ray_with_candidates + PER_TEST * c["tests"] + PER_NODE * c["nodes"]
-            + PER_DESCENT * c["descents"] + PER_BACKTRACK * c["backtracks"] + PER_HIT * c["hits"])
+    deeper = c["descents"] + c["backtracks"]
+    return (PER_RAY * n_ray_with_candidates + PER_BOUND * c["tests"] + PER_ROOT * (c["nodes"] - deeper)
+            + PER_NODE * deeper + PER_DESCENT * c["descents"] + PER_BACKTRACK * c["backtracks"]
+            + PER_HIT * c["hits"])
 
 
 def alg_bytes(n_ray, n_pair, n_piece_touched):

@@ -7,7 +7,9 @@ Two decisions:
   at the hit for at least 99.9 % of the depth-22 hits.  The method converges
   to its limit surface as the depth grows (Sec. 3.2); d* is where further
   subdivision no longer changes the result at that tolerance.
-* launch shape: the kernel variant (lane- or warp-per-ray), CTAs per SM and
+* math mode and launch shape: IEEE or approximate reciprocal / square
+  root (both within the parity tolerance), the kernel variant (lane- or warp-per-ray, or the two-phase
+  filter path), CTAs per SM and
   the warp's ray chunk, chosen by timing every candidate on the workload with
   CUDA events.  (The lane kernel's CTA is fixed at 128 threads.)
 
@@ -23,8 +25,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tune_cache.json")
-DEFAULT = {"depth": 10, "fast": False, "block": 128, "blocks_per_sm": 0, "chunk": 32, "variant": 1}
-VARIANTS = (1, 2)          # FX_VARIANT_LANE, FX_VARIANT_WARP
+DEFAULT = {"depth": 10, "fast": False, "block": 128, "blocks_per_sm": 0, "chunk": 32, "variant": 0}
+VARIANTS = (1, 2, 3)       # FX_VARIANT_LANE, FX_VARIANT_WARP, FX_VARIANT_FILTER
 BLOCKS_PER_SM = (0, 4, 5)  # 0: as many as fit
 CHUNKS = (8, 16, 32, 64)
 
@@ -98,19 +100,24 @@ def time_launch(fib, rays, row_ptr, seg_idx, depth, flags, reps=20):
     return a.elapsed_time(b) / reps
 
 
-def search_launch(fib, rays, row_ptr, seg_idx, depth, flags=0):
+def search_launch(fib, rays, row_ptr, seg_idx, depth, maths=(False, True)):
+    """Times every (math mode, variant, CTAs per SM, chunk); both math modes
+    meet the parity tolerance (the GPU tests check each), so the faster wins."""
     best = None
     table = []
-    for variant in VARIANTS:
-        for bps in BLOCKS_PER_SM:
-            for chunk in CHUNKS:
-                fib.set_launch(128, bps, chunk, variant)
-                ms = time_launch(fib, rays, row_ptr, seg_idx, depth, flags)
-                table.append((variant, bps, chunk, ms))
-                if best is None or ms < best[3]:
-                    best = (variant, bps, chunk, ms)
-    fib.set_launch(128, best[1], best[2], best[0])
-    return {"block": 128, "blocks_per_sm": best[1], "chunk": best[2], "variant": best[0], "ms": best[3]}, table
+    for fast in maths:
+        flags = 0x2 if fast else 0
+        for variant in VARIANTS:
+            for bps in BLOCKS_PER_SM:
+                for chunk in CHUNKS:
+                    fib.set_launch(128, bps, chunk, variant)
+                    ms = time_launch(fib, rays, row_ptr, seg_idx, depth, flags)
+                    table.append((int(fast), variant, bps, chunk, ms))
+                    if best is None or ms < best[4]:
+                        best = (int(fast), variant, bps, chunk, ms)
+    fib.set_launch(128, best[2], best[3], best[1])
+    return {"fast": bool(best[0]), "block": 128, "blocks_per_sm": best[2], "chunk": best[3],
+            "variant": best[1], "ms": best[4]}, table
 
 
 def tuned_config(fib, rays, row_ptr, seg_idx, retune=False, cps=None):
@@ -125,8 +132,7 @@ def tuned_config(fib, rays, row_ptr, seg_idx, retune=False, cps=None):
     if cps is not None:
         cfg["depth"], rep = select_depth(fib, rays, row_ptr, seg_idx, cps)
         cfg["depth_report"] = rep
-    launch, table = search_launch(fib, rays, row_ptr, seg_idx, cfg["depth"],
-                                  flags=(0x2 if cfg["fast"] else 0))
+    launch, table = search_launch(fib, rays, row_ptr, seg_idx, cfg["depth"])
     cfg.update(launch)
     cfg["table"] = table
     cache[key] = cfg

@@ -138,6 +138,49 @@ def test_depth_sweep(klass, forced, flags):
     fib.close()
 
 
+def _filter_vs_lane(case, depth, flags):
+    fib = F.Fibers(case["cps"])
+    assert fib.info()["n_piece"] == case["cps"].shape[0]  # single level-0 pieces: the filter applies
+    out = {}
+    for v in (F.FX_VARIANT_LANE, F.FX_VARIANT_FILTER):
+        fib.set_launch(variant=v)
+        fib.counters(reset=True)
+        tu, seg, leaf = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth,
+                                            flags | F.FX_COUNT)
+        torch.cuda.synchronize()
+        out[v] = (_np(tu), _np(seg), _np(leaf), fib.counters(reset=True), fib.status())
+    fib.close()
+    (tl, sl, ll, cl, stl), (tf, sf, lf, cf, stf) = out[F.FX_VARIANT_LANE], out[F.FX_VARIANT_FILTER]
+    assert stl == 0 and stf == 0
+    np.testing.assert_array_equal(sf, sl)
+    np.testing.assert_array_equal(lf, ll)
+    np.testing.assert_array_equal(tf, tl)
+    # the same traversals; the lane kernel rejects some candidates by their
+    # bound without a root node test, the filter tests every root
+    for k in ("tests", "descents", "backtracks", "hits"):
+        assert cf[k] == cl[k], (k, cf, cl)
+    assert cl["nodes"] <= cf["nodes"]
+    return sl
+
+
+@pytest.mark.parametrize("klass", ["straight", "moderate"])
+@pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+def test_filter_path_equals_lane_kernel(klass, forced, flags):
+    # both paths skip only candidates whose root test cannot pass and traverse
+    # the rest the same way: same hits, same traversal counters
+    case = I.sweep_case(klass, 4096, forced_hits=forced)
+    for depth in (0, 4, 10, 16, 22):
+        _filter_vs_lane(case, depth, flags)
+
+
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+def test_filter_path_equals_lane_kernel_on_hair(hair, flags):
+    case = hair[0]
+    seg = _filter_vs_lane(case, 15, flags)
+    assert (seg >= 0).sum() > 100_000
+
+
 @pytest.mark.parametrize("variant", VARIANTS, ids=["lane", "warp"])
 def test_counters_match_oracle(tiny, variant):
     # per-pair mode visits exactly the oracle's nodes (same decisions); the
