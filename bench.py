@@ -272,8 +272,6 @@ def main():
     depth = args.depth if args.depth is not None else cfg["depth"]
     fast = cfg["fast"] if args.fast is None else bool(args.fast)
     flags = (F.FX_FAST_MATH if fast else 0) | (F.FX_KERNEL_NAIVE if args.kernel == "naive" else 0)
-    fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"], cfg.get("variant", 0))
-
     tu = torch.empty((n_ray, 2), dtype=torch.float32, device=dev)
     seg = torch.empty(n_ray, dtype=torch.int32, device=dev)
     leaf = torch.empty(n_ray, dtype=torch.int32, device=dev)
@@ -282,10 +280,16 @@ def main():
     def step():
         F.intersect_closest(fib, rays, row_ptr, seg_idx, depth, flags, out=out)
 
-    # counters (untimed) for the algorithmic work of one launch
+    # counters (untimed) for the algorithmic work of one launch, taken on the
+    # lane kernel: it performs every root test as a node step (the scan
+    # variant tests most roots inside its warp-wide scans, where they are
+    # not counted as nodes); descents, backtracks, hits and pair tests are
+    # the same on both
+    fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"], F.FX_VARIANT_LANE)
     fib.counters(reset=True)
     F.intersect_closest(fib, rays, row_ptr, seg_idx, depth, flags | F.FX_COUNT, out=out)
     counters = fib.counters(reset=True)
+    fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"], cfg.get("variant", 0))
     n_ray_cand = int(np.count_nonzero(np.diff(case["row_ptr"])))
     n_piece_touched = int(len(np.unique(case["seg_idx"])))
     work = FL.alg_flops(counters, n_ray_cand)
@@ -304,7 +308,11 @@ def main():
         run = graph.replay
     else:
         run = step
-    launches_per_step = 2 if args.kernel == "naive" else 1
+    # kernels of ours per step: the naive path's pair kernel and resolve; the
+    # two-phase and scan variants' two kernels; one persistent kernel
+    # otherwise
+    two = fib.get_launch()["variant"] in (F.FX_VARIANT_FILTER, F.FX_VARIANT_SCAN)
+    launches_per_step = 2 if args.kernel == "naive" or two else 1
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     with torch.cuda.stream(stream):

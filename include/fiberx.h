@@ -89,6 +89,11 @@ typedef struct {
                                handles whose segments are single level-0 pieces (none pre-split
                                or unsupported) only; elsewhere LANE runs.  Its work lists
                                (8 B per pair, 8 B per ray) come from the handle's memory pool. */
+#define FX_VARIANT_SCAN 4   /* each lane owns a ray as in LANE; the warp tests 32 candidates of a
+                               lane's row at once (bound and root cylinder, one lane per
+                               candidate) and the owner traverses the root hits in row order.
+                               Same results as LANE.  Handles whose segments are single level-0
+                               pieces only; elsewhere LANE runs. */
 
 /* Launch configuration of the persistent kernels (fx_set_launch). */
 typedef struct {

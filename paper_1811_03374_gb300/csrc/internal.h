@@ -87,6 +87,19 @@ cudaError_t launch_lane_ray(const TraceArgs &a, bool pairs, uint32_t flags, int 
 cudaError_t launch_filter(const TraceArgs &a, const FilterArgs &o, uint32_t flags, int blocks_per_sm_cap,
                           int sm_count, cudaStream_t s);
 
+// Work list of the scan path (scan_kernels.cu), allocated per call: the rays
+// that have candidates, as {ray, row begin, row end, 0}.
+struct ScanArgs {
+  int4 *act;        // n_ray entries (the first *n_act used)
+  uint32_t *n_act;  // 1, zeroed before the rows pass runs
+};
+
+// scan_kernels.cu: rows pass (misses of rays without candidates, list of the
+// others), then lane-per-ray traversal with candidates scanned 32 at a time
+// by the warp (handles with single level-0 pieces only)
+cudaError_t launch_scan_ray(const TraceArgs &a, const ScanArgs &o, bool pairs, uint32_t flags,
+                            int blocks_per_sm_cap, int sm_count, cudaStream_t s);
+
 // warp_kernels.cu
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
                             int sm_count, cudaStream_t s);

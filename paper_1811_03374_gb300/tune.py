@@ -8,10 +8,11 @@ Two decisions:
   to its limit surface as the depth grows (Sec. 3.2); d* is where further
   subdivision no longer changes the result at that tolerance.
 * math mode and launch shape: IEEE or approximate reciprocal / square
-  root (both within the parity tolerance), the kernel variant (lane- or warp-per-ray, or the two-phase
-  filter path), CTAs per SM and
-  the warp's ray chunk, chosen by timing every candidate on the workload with
-  CUDA events.  (The lane kernel's CTA is fixed at 128 threads.)
+  root (both within the parity tolerance), the kernel variant (lane- or
+  warp-per-ray, the two-phase filter path, or the lane kernel with warp-wide
+  candidate scans), CTAs per SM and the warp's ray chunk, chosen by timing
+  every candidate on the workload with CUDA events.  (The persistent kernels'
+  CTAs are fixed at 128 threads.)
 
 Results are cached per (GPU name, workload signature) in tune_cache.json next
 to this file; a committed entry serves as the default.
@@ -26,9 +27,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tune_cache.json")
 DEFAULT = {"depth": 10, "fast": False, "block": 128, "blocks_per_sm": 0, "chunk": 32, "variant": 0}
-VARIANTS = (1, 2, 3)       # FX_VARIANT_LANE, FX_VARIANT_WARP, FX_VARIANT_FILTER
+VARIANTS = (1, 2, 3, 4)    # FX_VARIANT_LANE, FX_VARIANT_WARP, FX_VARIANT_FILTER, FX_VARIANT_SCAN
 BLOCKS_PER_SM = (0, 4, 5)  # 0: as many as fit
-CHUNKS = (8, 16, 32, 64)
+# rays a warp takes from the queue at a time; the filter and scan variants'
+# queues hold only rays with candidates, so they balance with small chunks
+CHUNKS = {1: (8, 16, 32, 64), 2: (8, 16, 32, 64), 3: (2, 4, 8, 32), 4: (1, 2, 4, 8)}
 
 
 def _key(fib, n_ray, n_pair):
@@ -109,7 +112,7 @@ def search_launch(fib, rays, row_ptr, seg_idx, depth, maths=(False, True)):
         flags = 0x2 if fast else 0
         for variant in VARIANTS:
             for bps in BLOCKS_PER_SM:
-                for chunk in CHUNKS:
+                for chunk in CHUNKS[variant]:
                     fib.set_launch(128, bps, chunk, variant)
                     ms = time_launch(fib, rays, row_ptr, seg_idx, depth, flags)
                     table.append((int(fast), variant, bps, chunk, ms))

@@ -181,6 +181,77 @@ def test_filter_path_equals_lane_kernel_on_hair(hair, flags):
     assert (seg >= 0).sum() > 100_000
 
 
+def _scan_vs_lane(case, depth, flags, pairs=False):
+    """The scan path against the lane kernel on one launch each: identical
+    outputs, the same candidates examined and the same traversals; the scan
+    drops candidates whose root cylinder misses before any node step."""
+    fib = F.Fibers(case["cps"])
+    assert fib.info()["n_piece"] == case["cps"].shape[0]  # single level-0 pieces: the scan applies
+    out = {}
+    for v in (F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN):
+        fib.set_launch(variant=v)
+        fib.counters(reset=True)
+        if pairs:
+            res = F.intersect_pairs(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth,
+                                    flags | F.FX_COUNT)
+        else:
+            res = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth,
+                                      flags | F.FX_COUNT)
+        torch.cuda.synchronize()
+        out[v] = ([_np(x) for x in res], fib.counters(reset=True), fib.status())
+    fib.close()
+    (rl, cl, stl), (rs, cs, sts) = out[F.FX_VARIANT_LANE], out[F.FX_VARIANT_SCAN]
+    assert stl == 0 and sts == 0
+    for a, b in zip(rl, rs):
+        np.testing.assert_array_equal(b, a)
+    for k in ("tests", "descents", "backtracks", "hits"):
+        assert cs[k] == cl[k], (k, cs, cl)
+    assert cs["nodes"] <= cl["nodes"]
+    return rs
+
+
+@pytest.mark.parametrize("klass", ["straight", "moderate"])  # the curved class is pre-split
+@pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+@pytest.mark.parametrize("pairs", [False, True], ids=["closest", "pairs"])
+def test_scan_path_equals_lane_kernel(klass, forced, flags, pairs):
+    case = I.sweep_case(klass, 4096, forced_hits=forced)
+    # one ray listing many segments: rows longer than a 32-candidate window,
+    # with a ragged last window
+    g = np.random.default_rng(3)
+    rows = [case["seg_idx"][case["row_ptr"][i]:case["row_ptr"][i + 1]] for i in range(len(case["rays"]))]
+    for i in range(0, len(rows), 97):
+        rows[i] = np.concatenate([rows[i], g.integers(0, case["cps"].shape[0], 1 + i % 150)]).astype(np.int32)
+    case = dict(case, seg_idx=np.concatenate(rows).astype(np.int32),
+                row_ptr=np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32))
+    for depth in (0, 4, 10, 16, 22):
+        _scan_vs_lane(case, depth, flags, pairs)
+
+
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+@pytest.mark.parametrize("pairs", [False, True], ids=["closest", "pairs"])
+def test_scan_path_equals_lane_kernel_on_hair(hair, flags, pairs):
+    case = hair[0]
+    depth = 15
+    if pairs:  # a seeded block of 20,000 rays with candidates
+        counts = np.diff(case["row_ptr"])
+        idx = np.nonzero(counts > 0)[0][::6][:20000]
+        case = I.subsample_rays(case, idx)
+    res = _scan_vs_lane(case, depth, flags, pairs)
+    if not pairs:
+        assert (res[1] >= 0).sum() > 100_000
+
+
+def test_scan_falls_back_on_presplit_handles(tiny):
+    # the tiny fibers are pre-split: the scan variant runs the lane kernel
+    case, pieces, ref = tiny
+    res = {}
+    for v in (F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN):
+        res[v] = _run_closest(case, 8, 0, variant=v)
+    for a, b in zip(res[F.FX_VARIANT_LANE], res[F.FX_VARIANT_SCAN]):
+        np.testing.assert_array_equal(np.asarray(b), np.asarray(a))
+
+
 @pytest.mark.parametrize("variant", VARIANTS, ids=["lane", "warp"])
 def test_counters_match_oracle(tiny, variant):
     # per-pair mode visits exactly the oracle's nodes (same decisions); the
@@ -233,9 +304,12 @@ def test_host_entry_matches_device(tiny):
     fib.close()
 
 
-def test_edge_cases():
+@pytest.mark.parametrize("variant", [F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN], ids=["lane", "scan"])
+def test_edge_cases(variant):
     case = I.sweep_case("moderate", 64, forced_hits=True)
     fib = F.Fibers(case["cps"])
+    assert fib.info()["n_piece"] == 64
+    fib.set_launch(variant=variant)
     # no rays
     tu, seg, _ = F.intersect_closest(fib, np.zeros((0, 8), np.float32), np.zeros(1, np.int32),
                                      np.zeros(0, np.int32), 8)
@@ -259,7 +333,7 @@ def test_edge_cases():
     # depth 0 (single cylinder) and 23 (finest)
     for d in (0, 23):
         ref = O.closest(case, d)
-        tu, seg, _, _ = _run_closest(case, d, 0, fib)
+        tu, seg, _, _ = _run_closest(case, d, 0, fib, variant=variant)
         stats = P.compare_closest(case, d, tu, seg, ref, O.presplit(case["cps"]))
         _assert_parity(stats, max_band_frac=0.05)
     # bad depth and bad sizes are refused before launch
@@ -293,24 +367,27 @@ def test_upload_rejects_bad_fibers():
 @pytest.fixture(scope="module")
 def hair():
     """The full hair-patch frame and the oracle on a seeded sample of 3000
-    rays that have candidates."""
+    rays that have candidates, at depth 10 and at the benchmark's depth 15."""
     case = I.hair_patch()
     counts = np.diff(case["row_ptr"])
     g = np.random.default_rng(5)
     idx = np.sort(g.choice(np.nonzero(counts > 0)[0], 3000, replace=False))
     sub = I.subsample_rays(case, idx)
     pieces = O.presplit(case["cps"])
-    ref = O.closest(sub, 10, pieces)
+    ref = {d: O.closest(sub, d, pieces) for d in (10, 15)}
     return case, idx, sub, pieces, ref
 
 
+@pytest.mark.parametrize("variant", [F.FX_VARIANT_AUTO, F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN],
+                         ids=["auto", "lane", "scan"])
+@pytest.mark.parametrize("depth", [10, 15])
 @pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
-def test_hair_patch_full_size_sampled(hair, flags):
+def test_hair_patch_full_size_sampled(hair, flags, depth, variant):
     # the benchmark's workload and launch: full frame on the GPU, oracle on the
     # sampled rays
-    case, idx, sub, pieces, ref = hair
-    depth = 10
-    tu, seg, leaf, st = _run_closest(case, depth, flags)
+    case, idx, sub, pieces, refs = hair
+    ref = refs[depth]
+    tu, seg, leaf, st = _run_closest(case, depth, flags, variant=variant)
     assert st & ~F.FX_DEV_UNSUPPORTED == 0
     counts = np.diff(case["row_ptr"])
     stats = P.compare_closest(sub, depth, tu[idx], seg[idx], ref, pieces, leaf[idx])
