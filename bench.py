@@ -146,26 +146,31 @@ def load_workload(rank=0):
     return case
 
 
-TRAFFIC_KEY = "k_lane_hair"
+# DRAM traffic per launch of the timed persistent kernel, from the committed
+# ncu summaries, by variant: (key in profiles/traffic.json, its sources)
+TRAFFIC = {1: ("k_lane_hair", ("trace.cuh", "lane_kernels.cu")),
+           4: ("k_scan_hair", ("trace.cuh", "scan_kernels.cu"))}
 
 
-def source_hash():
-    """Hash of the sources of the default kernel (traffic figures taken on
-    another version of it do not apply)."""
+def source_hash(files):
+    """Hash of a kernel's sources (traffic figures taken on another version
+    of it do not apply)."""
     h = hashlib.sha256()
-    for f in ("trace.cuh", "lane_kernels.cu"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1811_03374_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_name):
+def profiled_traffic(variant):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+    on the current source of the variant's kernel."""
+    if variant not in TRAFFIC:
+        return None
+    key, files = TRAFFIC[variant]
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        d = json.load(open(path))
-        e = d.get(kernel_name)
-        if e and e.get("source_hash") == source_hash():
+        e = json.load(open(path)).get(key)
+        if e and e.get("source_hash") == source_hash(files):
             return e.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -373,7 +378,7 @@ def main():
     sm = info["sm_count"]
     peak = FL.fp32_peak_tflops(sm, 2070.0)
     achieved = work / (ms_step * 1e-3) / 1e12
-    traffic = profiled_traffic(TRAFFIC_KEY)
+    traffic = profiled_traffic(fib.get_launch()["variant"]) if args.kernel == "persistent" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)" % sm,

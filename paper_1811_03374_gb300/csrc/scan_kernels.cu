@@ -4,15 +4,17 @@
 // Each lane owns one ray and traverses its candidates in row order with the
 // closest hit so far as t_max (instant termination, Sec. 3.2, carried across
 // candidates), as in the lane kernel.  What differs is how a lane finds its
-// next candidate worth traversing: the whole warp tests 32 consecutive
-// candidates of that lane's row at once, one candidate per lane -- a
-// coalesced load of 32 segment ids, a gather of their 32-byte root records,
-// the bound of the root node's capped cylinder against the ray's t_max, then
-// the root cylinder test itself (Sec. 3.3, unit ray against the cylinder of
-// the precomputed conservative radius).  A ballot turns the window into a
-// bit mask of candidates whose root cylinder is hit; the owner lane
-// traverses exactly those, in order.  Candidates rejected in the scan cost a
-// thirty-second of a warp step each instead of a full lane step.
+// next candidate worth traversing: the whole warp tests a window of 32
+// consecutive candidates of that lane's row at once, one candidate per lane
+// -- a coalesced load of 32 segment ids, their 32-byte root records copied
+// to shared memory, the bound of the root node's capped cylinder against the
+// ray's t_max, then the root cylinder test itself (Sec. 3.3, unit ray against
+// the cylinder of the precomputed conservative radius).  A ballot ranks the
+// candidates whose root cylinder is hit; the first kPL of them go, in row
+// order, to a short list of the owner's in shared memory (segment, the bound
+// test's left-hand side, root radius, candidate index), and if there are
+// more, the owner's row resumes at the next one.  Candidates rejected in the
+// scan cost a thirty-second of a warp step each instead of a full lane step.
 //
 // A rows pass runs first: it writes the misses of the rays without
 // candidates and lists the others (ray, row begin, row end), prefetching
@@ -23,17 +25,17 @@
 // that their memory latency overlaps the node steps of the other lanes:
 // iteration i loads the segment ids of up to kS new windows (one per hungry
 // lane), iteration i + 1 copies their root records into shared memory
-// (cp.async), iteration i + 2 tests them and hands out the masks.  When a
+// (cp.async), iteration i + 2 tests them and hands out the lists.  When a
 // ray is taken, its whole row of segment ids is prefetched into L2 with one
 // bulk prefetch.
 //
 // The scan tests a window against the ray's t_max at the time of the scan,
 // which is never smaller than at the time the owner traverses a candidate
 // of the window; before a traversal the owner repeats the bound test with
-// the current t_max, and the traversal starts with the full root test
-// (cylinder and end-plane slab).  So exactly the candidates that the lane
-// kernel traverses are traversed here, with the same t_max: the results are
-// the same bit for bit.
+// the current t_max (from the kept left-hand side: the same float), and the
+// traversal starts with the full root test (cylinder and end-plane slab).
+// So exactly the candidates that the lane kernel traverses are traversed
+// here, with the same t_max: the results are the same bit for bit.
 //
 // Handles whose segments are single level-0 pieces only (segment id = piece
 // id); others run the lane kernel.
@@ -53,14 +55,17 @@ constexpr int kScanBlock = 128;
 #endif
 // windows entering the scan pipeline per iteration (at most one per lane)
 constexpr int kS = FX_SCAN_S;
-static_assert(kS >= 1 && kS <= 8, "1 to 8 scans per round");
+static_assert(kS >= 1 && kS <= 8, "1 to 8 windows per iteration");
 // CTAs per SM the register budget is sized for (5: up to 102 registers)
 #ifndef FX_SCAN_MINB
 #define FX_SCAN_MINB 5
 #endif
 // root hits of a window handed to its owner at once; a window with more
 // resumes at the next one
-constexpr int kPL = 4;
+#ifndef FX_SCAN_PL
+#define FX_SCAN_PL 4
+#endif
+constexpr int kPL = FX_SCAN_PL;
 // relative slack of the bound test against FP32 rounding of the rotation
 // (the lane kernel uses the same)
 constexpr float kBoundSlack = 1.0f / 262144.0f;
