@@ -289,10 +289,11 @@ def main():
     # lane kernel: it performs every root test as a node step (the scan
     # variant tests most roots inside its warp-wide scans, where they are
     # not counted as nodes); descents, backtracks, hits and pair tests are
-    # the same on both
+    # the same on both.  The naive kernel is timed against the same work (it
+    # prunes nothing across candidates and so performs much more).
     fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"], F.FX_VARIANT_LANE)
     fib.counters(reset=True)
-    F.intersect_closest(fib, rays, row_ptr, seg_idx, depth, flags | F.FX_COUNT, out=out)
+    F.intersect_closest(fib, rays, row_ptr, seg_idx, depth, (flags & ~F.FX_KERNEL_NAIVE) | F.FX_COUNT, out=out)
     counters = fib.counters(reset=True)
     fib.set_launch(cfg["block"], cfg["blocks_per_sm"], cfg["chunk"], cfg.get("variant", 0))
     n_ray_cand = int(np.count_nonzero(np.diff(case["row_ptr"])))
@@ -377,11 +378,13 @@ def main():
 
     sm = info["sm_count"]
     peak = FL.fp32_peak_tflops(sm, 2070.0)
+    fma_tflops, _ = F.fma_peak()  # measured FP32 FMA throughput, the cross-check of `peak`
     achieved = work / (ms_step * 1e-3) / 1e12
     traffic = profiled_traffic(fib.get_launch()["variant"]) if args.kernel == "persistent" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)" % sm,
+                "fma_microbenchmark_tflops": fma_tflops,
                 "alg_flops_per_launch": work,
                 "hbm_gbs_algorithmic": abytes / (ms_step * 1e-3) / 1e9,
                 "alg_bytes_per_launch": abytes}

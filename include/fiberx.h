@@ -59,7 +59,7 @@ typedef enum {
 #define FX_KERNEL_PERSISTENT 0x0u /* default: persistent work-queue kernel */
 #define FX_KERNEL_NAIVE 0x1u      /* one thread per (ray, segment) pair (baseline) */
 #define FX_FAST_MATH 0x2u         /* approximate reciprocal / square root in the traversal */
-#define FX_POLISH_FP64 0x4u       /* re-evaluate each hit's leaf in FP64 (intersect_closest) */
+#define FX_POLISH_FP64 0x4u       /* re-evaluate each hit's leaf and its neighbours in FP64, keep the nearest (intersect_closest) */
 #define FX_COUNT 0x8u             /* accumulate node / descent / backtrack counters */
 #define FX_CHECK_INDEX 0x10u      /* range-check candidate segment ids on the device */
 
@@ -252,6 +252,18 @@ fx_status intersect_closest_noalloc(const fx_fibers *f, const float *rays, int64
                                     const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
                                     int32_t depth, uint32_t flags, float *tu, int32_t *seg,
                                     int32_t *leaf, void *stream);
+
+/*
+ * fx_fma_peak -- measures the FP32 FMA throughput of the current device: one
+ * launch of blocks_per_sm x 256-thread blocks per SM, each thread running
+ * eight independent FMA chains of 16 * iters steps, timed with CUDA events on
+ * `stream` (synchronises it).  *ms: the launch's time; *tflops: FMA flops
+ * (2 per FMA) per second / 1e12.  A measurement helper for the FP32 FMA
+ * roofline the traversal is reported against (the paper has no counterpart).
+ * Errors: FX_EINVAL (null outputs, blocks_per_sm outside 1..8, iters < 1),
+ * FX_ECUDA.
+ */
+fx_status fx_fma_peak(int32_t blocks_per_sm, int32_t iters, float *ms, double *tflops, void *stream);
 
 /* Text of the last error on this thread ("" if none). */
 const char *fx_last_error(void);

@@ -147,6 +147,18 @@ extern "C" {
 
 const char* fx_last_error(void) { return g_err.c_str(); }
 
+fx_status fx_fma_peak(int32_t blocks_per_sm, int32_t iters, float* ms, double* tflops, void* stream) {
+  if (!ms || !tflops) return fail(FX_EINVAL, "null output");
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1) return fail(FX_EINVAL, "blocks_per_sm or iters out of range");
+  int dev = 0, sms = 0;
+  FX_CUDA(cudaGetDevice(&dev));
+  FX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double flops = 0.0;
+  FX_CUDA(fx::fma_peak(sms, blocks_per_sm, iters, ms, &flops, (cudaStream_t)stream));
+  *tflops = flops / (*ms * 1e-3) / 1e12;
+  return FX_OK;
+}
+
 int32_t fx_version(void) { return 10000; }
 
 fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, const fx_upload_opts* opts,

@@ -104,6 +104,10 @@ cudaError_t launch_scan_ray(const TraceArgs &a, const ScanArgs &o, bool pairs, u
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
                             int sm_count, cudaStream_t s);
 
+// peak.cu: FP32 FMA microbenchmark (synchronises s); flops = FMA flops of the
+// timed launch
+cudaError_t fma_peak(int sm_count, int blocks_per_sm, int iters, float *ms, double *flops, cudaStream_t s);
+
 // fiberx_api.cu: text returned by fx_last_error() on this thread
 void set_last_error(const std::string &msg);
 

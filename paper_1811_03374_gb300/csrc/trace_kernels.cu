@@ -169,17 +169,105 @@ __device__ __forceinline__ double ddot3(const D4& a, const D4& b) {
   return a.x * b.x + a.y * b.y + a.z * b.z;
 }
 
-// The hit leaf's node recomputed in FP64 from the segment's control points in
-// the ray frame (Sec. 3.3 recomputation), its slab, conservative radius and
-// cylinder (App. A), giving t = max(c0, t_min) and u by projection.
+// Node of the leaf [u0, u0 + size] recomputed in FP64 from the segment's
+// control points Q in the ray frame (Sec. 3.3 recomputation), its slab,
+// conservative radius and cylinder (App. A): the entry t = max(c0, t_min)
+// into the capped leaf cylinder and u by projection; false if the ray misses
+// it within [0, tmax].
+__device__ bool polish_leaf(const D4 (&Q)[4], double u0, double size, double tmax, double& t_out,
+                            double& u_out) {
+  const double u1 = u0 + size;
+  auto eval = [&](double u) {
+    const double v = 1.0 - u, b0 = v * v * v, b1 = 3 * u * v * v, b2 = 3 * u * u * v, b3 = u * u * u;
+    return D4{b0 * Q[0].x + b1 * Q[1].x + b2 * Q[2].x + b3 * Q[3].x,
+              b0 * Q[0].y + b1 * Q[1].y + b2 * Q[2].y + b3 * Q[3].y,
+              b0 * Q[0].z + b1 * Q[1].z + b2 * Q[2].z + b3 * Q[3].z,
+              b0 * Q[0].w + b1 * Q[1].w + b2 * Q[2].w + b3 * Q[3].w};
+  };
+  auto deriv3 = [&](double u) {
+    const double v = 1.0 - u, b0 = v * v, b1 = 2 * u * v, b2 = u * u;
+    return D4{b0 * (Q[1].x - Q[0].x) + b1 * (Q[2].x - Q[1].x) + b2 * (Q[3].x - Q[2].x),
+              b0 * (Q[1].y - Q[0].y) + b1 * (Q[2].y - Q[1].y) + b2 * (Q[3].y - Q[2].y),
+              b0 * (Q[1].z - Q[0].z) + b1 * (Q[2].z - Q[1].z) + b2 * (Q[3].z - Q[2].z),
+              b0 * (Q[1].w - Q[0].w) + b1 * (Q[2].w - Q[1].w) + b2 * (Q[3].w - Q[2].w)};
+  };
+  const D4 cp0 = eval(u0), cp1 = eval(u1), g0 = deriv3(u0), g1 = deriv3(u1);
+  const D4 p = cp0;
+  const D4 d{cp1.x - cp0.x, cp1.y - cp0.y, cp1.z - cp0.z, cp1.w - cp0.w};
+  const D4 t0{size * g0.x, size * g0.y, size * g0.z, size * g0.w};
+  const D4 t1{size * g1.x, size * g1.y, size * g1.z, size * g1.w};
+  // slab
+  double lo = 0.0, hi = tmax;
+  if (t0.z != 0.0) {
+    const double t = ddot3(t0, p) / t0.z;
+    if (t0.z > 0.0) lo = fmax(lo, t); else hi = fmin(hi, t);
+  } else if (ddot3(t0, p) > 0.0) {
+    return false;
+  }
+  const D4 q{p.x + d.x, p.y + d.y, p.z + d.z, 0.0};
+  if (t1.z != 0.0) {
+    const double t = ddot3(t1, q) / t1.z;
+    if (t1.z < 0.0) lo = fmax(lo, t); else hi = fmin(hi, t);
+  } else if (ddot3(t1, q) < 0.0) {
+    return false;
+  }
+  // conservative radius
+  const double dd = ddot3(d, d);
+  double m;
+  if (dd > 0.0) {
+    const double b0 = ddot3(t0, d) / dd, b1 = ddot3(t1, d) / dd;
+    const double qx = t0.x - b0 * d.x, qy = t0.y - b0 * d.y, qz = t0.z - b0 * d.z;
+    const double sx = t1.x - b1 * d.x, sy = t1.y - b1 * d.y, sz = t1.z - b1 * d.z;
+    m = fmax(qx * qx + qy * qy + qz * qz, sx * sx + sy * sy + sz * sz);
+  } else {
+    m = fmax(ddot3(t0, t0), ddot3(t1, t1));
+  }
+  const double rad = sqrt(m) + p.w + fmax(fmax(0.0, t0.w), fmax(d.w, d.w - t1.w));
+  // cylinder
+  const double g = d.x * d.x + d.y * d.y;
+  double c0, c1;
+  if (g == 0.0) {
+    if (!(p.x * p.x + p.y * p.y < rad * rad)) return false;
+    c0 = -1e300;
+    c1 = 1e300;
+  } else {
+    const double cr = d.x * p.y - d.y * p.x;
+    const double e = rad * rad - cr * cr / g;
+    if (e < 0.0) return false;
+    const double tcpa = p.z - d.z * (d.x * p.x + d.y * p.y) / g;
+    const double sq = sqrt(e * (d.z * d.z + g) / g);
+    c0 = tcpa - sq;
+    c1 = tcpa + sq;
+  }
+  if (!(fmax(c0, lo) <= fmin(c1, hi))) return false;
+  t_out = fmax(c0, lo);
+  double ul = 0.0;
+  if (dd > 0.0) ul = fmin(1.0, fmax(0.0, (-p.x * d.x - p.y * d.y + (t_out - p.z) * d.z) / dd));
+  u_out = u0 + ul * size;
+  return true;
+}
+
+// FP64 re-evaluation of a hit: the FP32 traversal's leaf and its K
+// neighbours on either side (within the same piece) are recomputed in FP64
+// and the nearest entry is kept.  The FP32 traversal places a split plane
+// along the fiber only to within the FP32 spacing of ray-frame coordinates,
+// about 8 ulp(t) (they are differences from the ray origin, at the scale of
+// t); where leaves are shorter than that, or a split plane is nearly
+// parallel to the ray, the first leaf hit is a neighbour of the leaf it chose.
+// K = 2 + that spacing in leaf lengths, at most kPolishMaxK.  If FP64 hits
+// none of them, the FP32 result stays.
+constexpr int kPolishMaxK = 32;
+
 __global__ void __launch_bounds__(256) k_polish(const TraceArgs a, const float4* __restrict__ cp) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.n_ray) return;
   const int32_t s = a.seg[r];
   if (s < 0) return;
   const int32_t leaf = a.leaf[r];
-  // leaf size: 2^-max(depth, level of the piece holding the leaf)
+  // leaf size 2^-max(depth, level of the piece holding the leaf); the
+  // neighbours stay inside that piece's range of the segment
   int lvl = 0;
+  int64_t plo = 0, phi = kRootSize;
   if (!a.identity) {
     const int pb = __ldg(a.piece_begin + s), pe = __ldg(a.piece_begin + s + 1);
     for (int k = pb; k < pe; ++k) {
@@ -188,14 +276,16 @@ __global__ void __launch_bounds__(256) k_polish(const TraceArgs a, const float4*
       const int64_t lo = (int64_t)off << (23 - kl), hi = (int64_t)(off + 1) << (23 - kl);
       if (leaf >= lo && leaf < hi) {
         lvl = kl;
+        plo = lo;
+        phi = hi;
         break;
       }
     }
   }
   const int dl = a.depth > lvl ? a.depth : lvl;
-  const double size = (double)(1u << (23 - dl)) * (1.0 / 8388608.0);
-  const double u0 = (double)leaf * (1.0 / 8388608.0), u1 = u0 + size;
-  // ray frame in FP64 (Gram-Schmidt; any orthonormal frame gives the same result)
+  const int64_t isize = (int64_t)1 << (23 - dl);
+  const double size = (double)isize * (1.0 / 8388608.0);
+  // ray frame in FP64 (Duff et al.; any orthonormal frame gives the same result)
   const float4 ra = a.rays[2 * r], rb = a.rays[2 * r + 1];
   double w[3] = {rb.x, rb.y, rb.z};
   const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -217,73 +307,34 @@ __global__ void __launch_bounds__(256) k_polish(const TraceArgs a, const float4*
     Q[k].z = q0 * w[0] + q1 * w[1] + q2 * w[2];
     Q[k].w = P.w;
   }
-  auto eval = [&](double u) {
-    const double v = 1.0 - u, b0 = v * v * v, b1 = 3 * u * v * v, b2 = 3 * u * u * v, b3 = u * u * u;
-    return D4{b0 * Q[0].x + b1 * Q[1].x + b2 * Q[2].x + b3 * Q[3].x,
-              b0 * Q[0].y + b1 * Q[1].y + b2 * Q[2].y + b3 * Q[3].y,
-              b0 * Q[0].z + b1 * Q[1].z + b2 * Q[2].z + b3 * Q[3].z,
-              b0 * Q[0].w + b1 * Q[1].w + b2 * Q[2].w + b3 * Q[3].w};
-  };
-  auto deriv3 = [&](double u) {
-    const double v = 1.0 - u, b0 = v * v, b1 = 2 * u * v, b2 = u * u;
-    return D4{b0 * (Q[1].x - Q[0].x) + b1 * (Q[2].x - Q[1].x) + b2 * (Q[3].x - Q[2].x),
-              b0 * (Q[1].y - Q[0].y) + b1 * (Q[2].y - Q[1].y) + b2 * (Q[3].y - Q[2].y),
-              b0 * (Q[1].z - Q[0].z) + b1 * (Q[2].z - Q[1].z) + b2 * (Q[3].z - Q[2].z),
-              b0 * (Q[1].w - Q[0].w) + b1 * (Q[2].w - Q[1].w) + b2 * (Q[3].w - Q[2].w)};
-  };
-  const D4 cp0 = eval(u0), cp1 = eval(u1), g0 = deriv3(u0), g1 = deriv3(u1);
-  const D4 p = cp0;
-  const D4 d{cp1.x - cp0.x, cp1.y - cp0.y, cp1.z - cp0.z, cp1.w - cp0.w};
-  const D4 t0{size * g0.x, size * g0.y, size * g0.z, size * g0.w};
-  const D4 t1{size * g1.x, size * g1.y, size * g1.z, size * g1.w};
-  // slab
-  double lo = 0.0, hi = ra.w;
-  if (t0.z != 0.0) {
-    const double t = ddot3(t0, p) / t0.z;
-    if (t0.z > 0.0) lo = fmax(lo, t); else hi = fmin(hi, t);
-  } else if (ddot3(t0, p) > 0.0) {
-    lo = 1e300;
+  // leaf length in world units at the chosen leaf (|c'| = 3 |deriv3|)
+  double leaf_len;
+  {
+    const double um = ((double)leaf + 0.5 * (double)isize) * (1.0 / 8388608.0), v = 1.0 - um;
+    const double b0 = v * v, b1 = 2 * um * v, b2 = um * um;
+    const double dx = b0 * (Q[1].x - Q[0].x) + b1 * (Q[2].x - Q[1].x) + b2 * (Q[3].x - Q[2].x);
+    const double dy = b0 * (Q[1].y - Q[0].y) + b1 * (Q[2].y - Q[1].y) + b2 * (Q[3].y - Q[2].y);
+    const double dz = b0 * (Q[1].z - Q[0].z) + b1 * (Q[2].z - Q[1].z) + b2 * (Q[3].z - Q[2].z);
+    leaf_len = 3.0 * sqrt(dx * dx + dy * dy + dz * dz) * size;
   }
-  const D4 q{p.x + d.x, p.y + d.y, p.z + d.z, 0.0};
-  if (t1.z != 0.0) {
-    const double t = ddot3(t1, q) / t1.z;
-    if (t1.z < 0.0) lo = fmax(lo, t); else hi = fmin(hi, t);
-  } else if (ddot3(t1, q) < 0.0) {
-    lo = 1e300;
+  const double spacing = 8.0 * 0x1p-24 * fmax((double)a.tu[r].x, 1e-30);
+  int K = kPolishMaxK;
+  if (leaf_len > 0.0 && spacing / leaf_len < (double)kPolishMaxK) K = min(kPolishMaxK, 2 + (int)ceil(spacing / leaf_len));
+  double best_t = 1e300, best_u = 0.0;
+  int64_t best_leaf = -1;
+  for (int k = -K; k <= K; ++k) {
+    const int64_t start = (int64_t)leaf + k * isize;
+    if (start < plo || start + isize > phi) continue;
+    double t, u;
+    if (polish_leaf(Q, (double)start * (1.0 / 8388608.0), size, ra.w, t, u) && t < best_t) {
+      best_t = t;
+      best_u = u;
+      best_leaf = start;
+    }
   }
-  // conservative radius
-  const double dd = ddot3(d, d);
-  double m;
-  if (dd > 0.0) {
-    const double b0 = ddot3(t0, d) / dd, b1 = ddot3(t1, d) / dd;
-    const double qx = t0.x - b0 * d.x, qy = t0.y - b0 * d.y, qz = t0.z - b0 * d.z;
-    const double sx = t1.x - b1 * d.x, sy = t1.y - b1 * d.y, sz = t1.z - b1 * d.z;
-    m = fmax(qx * qx + qy * qy + qz * qz, sx * sx + sy * sy + sz * sz);
-  } else {
-    m = fmax(ddot3(t0, t0), ddot3(t1, t1));
-  }
-  const double rad = sqrt(m) + p.w + fmax(fmax(0.0, t0.w), fmax(d.w, d.w - t1.w));
-  // cylinder
-  const double g = d.x * d.x + d.y * d.y;
-  double c0, c1;
-  if (g == 0.0) {
-    if (!(p.x * p.x + p.y * p.y < rad * rad)) return;
-    c0 = -1e300;
-    c1 = 1e300;
-  } else {
-    const double cr = d.x * p.y - d.y * p.x;
-    const double e = rad * rad - cr * cr / g;
-    if (e < 0.0) return;  // FP32 and FP64 disagree on the leaf: keep the FP32 value
-    const double tcpa = p.z - d.z * (d.x * p.x + d.y * p.y) / g;
-    const double sq = sqrt(e * (d.z * d.z + g) / g);
-    c0 = tcpa - sq;
-    c1 = tcpa + sq;
-  }
-  if (!(fmax(c0, lo) <= fmin(c1, hi))) return;
-  const double t = fmax(c0, lo);
-  double ul = 0.0;
-  if (dd > 0.0) ul = fmin(1.0, fmax(0.0, (-p.x * d.x - p.y * d.y + (t - p.z) * d.z) / dd));
-  a.tu[r] = make_float2((float)t, (float)(u0 + ul * size));
+  if (best_leaf < 0) return;
+  a.tu[r] = make_float2((float)best_t, (float)best_u);
+  a.leaf[r] = (int32_t)best_leaf;
 }
 
 // ---------------------------------------------------------------------------

@@ -39,7 +39,7 @@ FX_VARIANT_SCAN = 4
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
            "intersect_backward", "intersect_closest_host", "intersect_closest_noalloc", "fx_set_launch",
-           "fx_get_launch", "fx_counters", "fx_stream_status", "fx_last_error", "fx_version"]
+           "fx_get_launch", "fx_counters", "fx_stream_status", "fx_fma_peak", "fx_last_error", "fx_version"]
 NOALLOC_MAX_RAYS = 1 << 20
 
 
@@ -108,6 +108,8 @@ def lib():
             L.fx_counters.restype = i32
             L.fx_stream_status.argtypes = [vp, vp, ctypes.POINTER(u32)]
             L.fx_stream_status.restype = i32
+            L.fx_fma_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double), vp]
+            L.fx_fma_peak.restype = i32
             L.fx_last_error.argtypes = []
             L.fx_last_error.restype = ctypes.c_char_p
             L.fx_version.argtypes = []
@@ -215,6 +217,14 @@ def _inputs(fibers, rays, row_ptr, seg_idx):
     if row_ptr.numel() != rays.shape[0] + 1:
         raise ValueError("row_ptr must have n_ray + 1 entries")
     return rays, row_ptr, seg_idx
+
+
+def fma_peak(blocks_per_sm=4, iters=4096, stream=None):
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms of
+    the timed launch)."""
+    ms, tf = ctypes.c_float(), ctypes.c_double()
+    _check(lib().fx_fma_peak(blocks_per_sm, iters, ctypes.byref(ms), ctypes.byref(tf), _stream(stream)))
+    return tf.value, ms.value
 
 
 def intersect_closest(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, stream=None,

@@ -19,8 +19,12 @@ computation can resolve a decision (a silhouette, a split plane, an end
 plane) or place a hit (for a ray nearly parallel to a fiber a sideways
 error e moves the hit along the fiber by e / tan(angle)).  A ray passes "in
 band" if the oracle result of one shifted copy (shifts of delta * 2^-k,
-k = 0..8, in 8 directions; the shifted rays are passed in double precision)
-meets the strict rule.
+k = 0..16, in 8 directions; the shifted rays are passed in double precision)
+meets the strict rule.  The small shifts matter far from the origin: there
+the difference of a control point and a ray origin is exact in FP32 and the
+decisions are resolved far below the |o| term of delta, yet a ray nearly
+parallel to a fiber still moves its hit along the fiber by (its sideways
+error) / tan(angle).
 
 Finally a ray is exempt ("silhouette") if it passes within 1e-4 r of the
 silhouette of the leaf cylinder hit by either side: |dist(ray, leaf axis) -
@@ -28,6 +32,9 @@ r_leaf| < 1e-4 r_leaf, measured in FP64 between the ray line and the leaf's
 axis line.  There the hit is ill-conditioned (grazing) and hit/miss, t and u
 may all legitimately differ.  Every other ray is a failure.
 """
+import json
+import os
+
 import numpy as np
 
 import oracle as O
@@ -80,12 +87,12 @@ def _perp(w):
     return e1, e2
 
 
-SCALES = tuple(2.0 ** -k for k in range(9))
+SCALES = tuple(2.0 ** -k for k in range(17))
 
 
 def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
     """Indices (subset of idx) whose GPU result the oracle reproduces for a
-    sideways-shifted copy of the ray: shifts of delta * 4^-k (k = 0..4) in
+    sideways-shifted copy of the ray: shifts of delta * 2^-k (k = 0..16) in
     8 directions orthogonal to the ray.  Near a silhouette the result moves
     like the square root of the shift, so several magnitudes are tried."""
     if len(idx) == 0:
@@ -191,3 +198,12 @@ def pairs_min(pr, case):
             if np.isfinite(pr["t"][j]):
                 t[i], u[i], s[i] = pr["t"][j], pr["u"][j], case["seg_idx"][j]
     return dict(t=t, u=u, seg=s)
+
+
+def report(rec):
+    """Appends one JSON line to the file named by FX_REPORT, if set (the
+    figures a run measured, for the design notes)."""
+    path = os.environ.get("FX_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")

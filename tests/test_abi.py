@@ -48,6 +48,10 @@ def test_argument_errors_without_device():
     assert L.fiber_info(None, None) == -1
     assert L.fx_stream_status(None, None, None) == -1
     assert b"null" in L.fx_last_error()
+    ms, tf = ctypes.c_float(), ctypes.c_double()
+    assert L.fx_fma_peak(4, 16, None, None, None) == -1
+    assert L.fx_fma_peak(0, 16, ctypes.byref(ms), ctypes.byref(tf), None) == -1
+    assert L.fx_fma_peak(4, 0, ctypes.byref(ms), ctypes.byref(tf), None) == -1
     L.fiber_free(None)  # no-op
 
 

@@ -132,6 +132,10 @@ def test_depth_sweep(klass, forced, flags):
         stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
         _assert_parity(stats, where="%s depth %d" % (klass, depth))
         worst = max(worst, stats["max_rel_t"])
+        P.report(dict(test="depth_sweep", klass=klass, forced=forced, math="fast" if flags else "ieee",
+                      depth=depth, n=stats["n"], hits=stats["hits"], strict=stats["strict"], band=stats["band"],
+                      silhouette=stats["silhouette"], max_rel_t=stats["max_rel_t"],
+                      median_rel_t=stats["med_rel_t"], max_du=stats["max_du"]))
         if forced:
             assert stats["hits"] > 3500
     assert fib.status() == 0
