@@ -323,6 +323,26 @@ def sweep_case(klass: str, n: int, seed: int = SEED_BASE + 2, forced_hits: bool 
                 name="sweep_%s" % klass)
 
 
+def single_fiber_case(klass: str, n_ray: int, seed: int = SEED_BASE + 5):
+    """One segment of the curvature class against n_ray rays, each aimed at a
+    uniform point of the segment's radius-dilated control-hull AABB from 10
+    segment lengths away in a uniform direction: the shape of the paper's own
+    benchmark (Fig. 1: about a million rays against a single fiber), whose
+    three fibers are given only as images."""
+    g = rng(seed + 7919 * list(SWEEP_JITTER).index(klass))
+    cps = sweep_segments(g, 1, SWEEP_JITTER[klass])
+    c64 = cps.astype(np.float64)[0]
+    rmax = c64[:, 3].max()
+    lo = c64[:, :3].min(axis=0) - rmax
+    hi = c64[:, :3].max(axis=0) + rmax
+    target = lo + (hi - lo) * g.uniform(0.0, 1.0, (n_ray, 3))
+    w = _unit_sphere(g, n_ray)
+    rays = pack_rays(target - 10.0 * w, w)
+    row_ptr = np.arange(n_ray + 1, dtype=np.int32)
+    seg_idx = np.zeros(n_ray, dtype=np.int32)
+    return dict(cps=cps, rays=rays, row_ptr=row_ptr, seg_idx=seg_idx, name="single_%s" % klass)
+
+
 # --------------------------------------------------------------------------
 # workload 3: precision stress
 # --------------------------------------------------------------------------

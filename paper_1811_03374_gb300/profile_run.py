@@ -6,8 +6,9 @@
 Workloads: hair (the 1080p hair-patch frame), tiny (16 fibers x 16,384
 rays), sweep-<class> (1M segments, one ray each, aimed at the segment's
 box), aimed-hair (1M rays aimed inside segments of 2000 hair fibers, the
-differentiation workload).  Prints the mean launch time measured with CUDA
-events after one untimed launch.
+differentiation workload), single-<class> (one segment of the class against
+2^20 rays aimed at its box: the shape of the paper's Fig. 1).  Prints the
+mean launch time measured with CUDA events after one untimed launch.
 
     --depths 2-22      one JSON line per depth in the range
     --backward 1       also times the adjoint (intersect_backward) of the
@@ -34,6 +35,8 @@ def load(name):
         return I.sweep_case(name.split("-", 1)[1], 1_000_000)
     if name == "aimed-hair":
         return I.aimed_hair_case(1_000_000)
+    if name.startswith("single-"):
+        return I.single_fiber_case(name.split("-", 1)[1], 1 << 20)
     raise SystemExit("unknown workload %s" % name)
 
 

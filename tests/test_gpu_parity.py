@@ -142,6 +142,21 @@ def test_depth_sweep(klass, forced, flags):
     fib.close()
 
 
+@pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
+def test_single_fiber_many_rays(klass):
+    # the shape of the paper's own benchmark: one fiber, many rays
+    case = I.single_fiber_case(klass, 8192)
+    pieces = O.presplit(case["cps"])
+    fib = F.Fibers(case["cps"])
+    for depth in (2, 8, 15, 22):
+        ref = O.closest(case, depth, pieces)
+        tu, seg, leaf, _ = _run_closest(case, depth, F.FX_FAST_MATH, fib)
+        stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
+        _assert_parity(stats, where="single %s depth %d" % (klass, depth))
+    assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
+    fib.close()
+
+
 def _filter_vs_lane(case, depth, flags):
     fib = F.Fibers(case["cps"])
     assert fib.info()["n_piece"] == case["cps"].shape[0]  # single level-0 pieces: the filter applies

@@ -62,3 +62,12 @@ def test_sweep_and_stress_cases():
     assert np.abs(g["delta"]).max() <= 1e-3
     o = I.offset_case(100, 1e4)
     assert np.abs(o["cps"][:, :, :3]).min() > 5e3
+
+
+def test_single_fiber_case():
+    for k in I.SWEEP_JITTER:
+        c = I.single_fiber_case(k, 1000)
+        assert c["cps"].shape == (1, 4, 4) and c["rays"].shape == (1000, 8)
+        assert np.all(c["seg_idx"] == 0) and c["row_ptr"][-1] == 1000
+        w = c["rays"][:, 4:7].astype(np.float64)
+        np.testing.assert_allclose(np.linalg.norm(w, axis=1), 1.0, rtol=1e-6)
