@@ -94,6 +94,11 @@ typedef struct {
                                candidate) and the owner traverses the root hits in row order.
                                Same results as LANE.  Handles whose segments are single level-0
                                pieces only; elsewhere LANE runs. */
+#define FX_VARIANT_RAY 5    /* one thread per ray walking its candidates in row order with LANE's
+                               arithmetic, no work queue: for rows of one or a few candidates
+                               (many rays against one fiber).  Same results as LANE.  Handles
+                               whose segments are single level-0 pieces only; elsewhere LANE
+                               runs. */
 
 /* Launch configuration of the persistent kernels (fx_set_launch). */
 typedef struct {

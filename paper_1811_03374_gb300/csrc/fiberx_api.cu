@@ -93,8 +93,8 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
   if (variant == FX_VARIANT_AUTO) variant = FX_VARIANT_LANE;
   // the two-phase path covers closest hits on handles of single level-0 pieces
   if (variant == FX_VARIANT_FILTER && (pairs || !f->identity)) variant = FX_VARIANT_LANE;
-  // the scan path covers handles of single level-0 pieces
-  if (variant == FX_VARIANT_SCAN && !f->identity) variant = FX_VARIANT_LANE;
+  // the scan and per-ray paths cover handles of single level-0 pieces
+  if ((variant == FX_VARIANT_SCAN || variant == FX_VARIANT_RAY) && !f->identity) variant = FX_VARIANT_LANE;
   if (variant == FX_VARIANT_FILTER) {
     int2* pass = nullptr;
     int32_t* ibuf = nullptr;
@@ -116,6 +116,8 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
   }
   if (variant == FX_VARIANT_WARP) {
     FX_CUDA(fx::launch_warp_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
+  } else if (variant == FX_VARIANT_RAY) {
+    FX_CUDA(fx::launch_ray(a, pairs, flags, s));
   } else if (variant == FX_VARIANT_SCAN) {
     int4* act = nullptr;
     FX_CUDA(cudaMallocFromPoolAsync((void**)&act, sizeof(int4) * (size_t)(a.n_ray + 1), f->pool, s));
@@ -303,7 +305,7 @@ fx_status fx_set_launch(fx_fibers* f, const fx_launch* cfg) {
   if (!(b == 64 || b == 128 || b == 256)) return fail(FX_EINVAL, "block must be 64, 128 or 256");
   if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 16) return fail(FX_EINVAL, "blocks_per_sm outside [0, 16]");
   if (cfg->chunk < 1 || cfg->chunk > 1024) return fail(FX_EINVAL, "chunk outside [1, 1024]");
-  if (cfg->variant < FX_VARIANT_AUTO || cfg->variant > FX_VARIANT_SCAN) return fail(FX_EINVAL, "unknown variant");
+  if (cfg->variant < FX_VARIANT_AUTO || cfg->variant > FX_VARIANT_RAY) return fail(FX_EINVAL, "unknown variant");
   f->launch = *cfg;
   return FX_OK;
 }

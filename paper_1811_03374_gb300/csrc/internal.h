@@ -100,6 +100,9 @@ struct ScanArgs {
 cudaError_t launch_scan_ray(const TraceArgs &a, const ScanArgs &o, bool pairs, uint32_t flags,
                             int blocks_per_sm_cap, int sm_count, cudaStream_t s);
 
+// ray_kernels.cu: one thread per ray (handles with single level-0 pieces only)
+cudaError_t launch_ray(const TraceArgs &a, bool pairs, uint32_t flags, cudaStream_t s);
+
 // warp_kernels.cu
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
                             int sm_count, cudaStream_t s);

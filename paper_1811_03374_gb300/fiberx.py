@@ -35,6 +35,7 @@ FX_VARIANT_LANE = 1
 FX_VARIANT_WARP = 2
 FX_VARIANT_FILTER = 3
 FX_VARIANT_SCAN = 4
+FX_VARIANT_RAY = 5
 
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",

@@ -52,7 +52,7 @@ def main():
     p.add_argument("--workload", default="hair")
     p.add_argument("--depth", type=int, default=10)
     p.add_argument("--depths", default=None, help="a range a-b or a list a,b,c of depths")
-    p.add_argument("--variant", default="auto", choices=["auto", "lane", "warp", "filter", "scan"])
+    p.add_argument("--variant", default="auto", choices=["auto", "lane", "warp", "filter", "scan", "ray"])
     p.add_argument("--kernel", default="persistent", choices=["persistent", "naive"])
     p.add_argument("--fast", type=int, default=1)
     p.add_argument("--block", type=int, default=128)
@@ -67,7 +67,7 @@ def main():
     case = load(a.workload)
     dev = torch.device("cuda")
     fib = F.Fibers(case["cps"])
-    fib.set_launch(a.block, 0, a.chunk, {"auto": 0, "lane": 1, "warp": 2, "filter": 3, "scan": 4}[a.variant])
+    fib.set_launch(a.block, 0, a.chunk, {"auto": 0, "lane": 1, "warp": 2, "filter": 3, "scan": 4, "ray": 5}[a.variant])
     rays = torch.from_numpy(case["rays"]).to(dev)
     rp = torch.from_numpy(case["row_ptr"]).to(dev)
     si = torch.from_numpy(case["seg_idx"]).to(dev)

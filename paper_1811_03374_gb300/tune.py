@@ -9,8 +9,9 @@ Two decisions:
   subdivision no longer changes the result at that tolerance.
 * math mode and launch shape: IEEE or approximate reciprocal / square
   root (both within the parity tolerance), the kernel variant (lane- or
-  warp-per-ray, the two-phase filter path, or the lane kernel with warp-wide
-  candidate scans), CTAs per SM and the warp's ray chunk, chosen by timing
+  warp-per-ray, the two-phase filter path, the lane kernel with warp-wide
+  candidate scans, or one thread per ray), CTAs per SM and the warp's ray
+  chunk, chosen by timing
   every candidate on the workload with CUDA events.  (The persistent kernels'
   CTAs are fixed at 128 threads.)
 
@@ -27,11 +28,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tune_cache.json")
 DEFAULT = {"depth": 10, "fast": False, "block": 128, "blocks_per_sm": 0, "chunk": 32, "variant": 0}
-VARIANTS = (1, 2, 3, 4)    # FX_VARIANT_LANE, FX_VARIANT_WARP, FX_VARIANT_FILTER, FX_VARIANT_SCAN
+VARIANTS = (1, 2, 3, 4, 5)  # FX_VARIANT_LANE, _WARP, _FILTER, _SCAN, _RAY
 BLOCKS_PER_SM = (0, 4, 5)  # 0: as many as fit
 # rays a warp takes from the queue at a time; the filter and scan variants'
 # queues hold only rays with candidates, so they balance with small chunks
-CHUNKS = {1: (8, 16, 32, 64), 2: (8, 16, 32, 64), 3: (2, 4, 8, 32), 4: (1, 2, 4, 8)}
+CHUNKS = {1: (8, 16, 32, 64), 2: (8, 16, 32, 64), 3: (2, 4, 8, 32), 4: (1, 2, 4, 8), 5: (32,)}
 
 
 def _key(fib, n_ray, n_pair):
@@ -111,7 +112,7 @@ def search_launch(fib, rays, row_ptr, seg_idx, depth, maths=(False, True)):
     for fast in maths:
         flags = 0x2 if fast else 0
         for variant in VARIANTS:
-            for bps in BLOCKS_PER_SM:
+            for bps in (BLOCKS_PER_SM if variant != 5 else (0,)):  # the per-ray kernel sizes its own grid
                 for chunk in CHUNKS[variant]:
                     fib.set_launch(128, bps, chunk, variant)
                     ms = time_launch(fib, rays, row_ptr, seg_idx, depth, flags)

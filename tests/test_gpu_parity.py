@@ -200,14 +200,15 @@ def test_filter_path_equals_lane_kernel_on_hair(hair, flags):
     assert (seg >= 0).sum() > 100_000
 
 
-def _scan_vs_lane(case, depth, flags, pairs=False):
-    """The scan path against the lane kernel on one launch each: identical
-    outputs, the same candidates examined and the same traversals; the scan
-    drops candidates whose root cylinder misses before any node step."""
+def _variant_vs_lane(case, depth, flags, pairs=False, variant=F.FX_VARIANT_SCAN):
+    """A variant against the lane kernel on one launch each: identical
+    outputs, the same candidates examined and the same traversals (the scan
+    variant drops candidates whose root cylinder misses before any node
+    step, so it counts fewer node tests)."""
     fib = F.Fibers(case["cps"])
-    assert fib.info()["n_piece"] == case["cps"].shape[0]  # single level-0 pieces: the scan applies
+    assert fib.info()["n_piece"] == case["cps"].shape[0]  # single level-0 pieces: the variant applies
     out = {}
-    for v in (F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN):
+    for v in (F.FX_VARIANT_LANE, variant):
         fib.set_launch(variant=v)
         fib.counters(reset=True)
         if pairs:
@@ -219,7 +220,7 @@ def _scan_vs_lane(case, depth, flags, pairs=False):
         torch.cuda.synchronize()
         out[v] = ([_np(x) for x in res], fib.counters(reset=True), fib.status())
     fib.close()
-    (rl, cl, stl), (rs, cs, sts) = out[F.FX_VARIANT_LANE], out[F.FX_VARIANT_SCAN]
+    (rl, cl, stl), (rs, cs, sts) = out[F.FX_VARIANT_LANE], out[variant]
     assert stl == 0 and sts == 0
     for a, b in zip(rl, rs):
         np.testing.assert_array_equal(b, a)
@@ -229,11 +230,15 @@ def _scan_vs_lane(case, depth, flags, pairs=False):
     return rs
 
 
+VARIANTS_EXACT = [F.FX_VARIANT_SCAN, F.FX_VARIANT_RAY]
+
+
+@pytest.mark.parametrize("variant", VARIANTS_EXACT, ids=["scan", "ray"])
 @pytest.mark.parametrize("klass", ["straight", "moderate"])  # the curved class is pre-split
 @pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
 @pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
 @pytest.mark.parametrize("pairs", [False, True], ids=["closest", "pairs"])
-def test_scan_path_equals_lane_kernel(klass, forced, flags, pairs):
+def test_variant_equals_lane_kernel(klass, forced, flags, pairs, variant):
     case = I.sweep_case(klass, 4096, forced_hits=forced)
     # one ray listing many segments: rows longer than a 32-candidate window,
     # with a ragged last window
@@ -244,30 +249,41 @@ def test_scan_path_equals_lane_kernel(klass, forced, flags, pairs):
     case = dict(case, seg_idx=np.concatenate(rows).astype(np.int32),
                 row_ptr=np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32))
     for depth in (0, 4, 10, 16, 22):
-        _scan_vs_lane(case, depth, flags, pairs)
+        _variant_vs_lane(case, depth, flags, pairs, variant)
 
 
+@pytest.mark.parametrize("variant", VARIANTS_EXACT, ids=["scan", "ray"])
 @pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
 @pytest.mark.parametrize("pairs", [False, True], ids=["closest", "pairs"])
-def test_scan_path_equals_lane_kernel_on_hair(hair, flags, pairs):
+def test_variant_equals_lane_kernel_on_hair(hair, flags, pairs, variant):
     case = hair[0]
     depth = 15
     if pairs:  # a seeded block of 20,000 rays with candidates
         counts = np.diff(case["row_ptr"])
         idx = np.nonzero(counts > 0)[0][::6][:20000]
         case = I.subsample_rays(case, idx)
-    res = _scan_vs_lane(case, depth, flags, pairs)
+    res = _variant_vs_lane(case, depth, flags, pairs, variant)
     if not pairs:
         assert (res[1] >= 0).sum() > 100_000
 
 
-def test_scan_falls_back_on_presplit_handles(tiny):
-    # the tiny fibers are pre-split: the scan variant runs the lane kernel
+@pytest.mark.parametrize("variant", VARIANTS_EXACT, ids=["scan", "ray"])
+@pytest.mark.parametrize("klass", ["straight", "moderate"])
+def test_variant_equals_lane_kernel_on_single_fiber(klass, variant):
+    case = I.single_fiber_case(klass, 1 << 16)
+    for depth in (2, 15, 22):
+        for pairs in (False, True):
+            _variant_vs_lane(case, depth, F.FX_FAST_MATH, pairs, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS_EXACT, ids=["scan", "ray"])
+def test_variant_falls_back_on_presplit_handles(tiny, variant):
+    # the tiny fibers are pre-split: the scan and per-ray variants run the lane kernel
     case, pieces, ref = tiny
     res = {}
-    for v in (F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN):
+    for v in (F.FX_VARIANT_LANE, variant):
         res[v] = _run_closest(case, 8, 0, variant=v)
-    for a, b in zip(res[F.FX_VARIANT_LANE], res[F.FX_VARIANT_SCAN]):
+    for a, b in zip(res[F.FX_VARIANT_LANE], res[variant]):
         np.testing.assert_array_equal(np.asarray(b), np.asarray(a))
 
 
@@ -323,7 +339,8 @@ def test_host_entry_matches_device(tiny):
     fib.close()
 
 
-@pytest.mark.parametrize("variant", [F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN], ids=["lane", "scan"])
+@pytest.mark.parametrize("variant", [F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN, F.FX_VARIANT_RAY],
+                         ids=["lane", "scan", "ray"])
 def test_edge_cases(variant):
     case = I.sweep_case("moderate", 64, forced_hits=True)
     fib = F.Fibers(case["cps"])
@@ -397,8 +414,8 @@ def hair():
     return case, idx, sub, pieces, ref
 
 
-@pytest.mark.parametrize("variant", [F.FX_VARIANT_AUTO, F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN],
-                         ids=["auto", "lane", "scan"])
+@pytest.mark.parametrize("variant", [F.FX_VARIANT_AUTO, F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN, F.FX_VARIANT_RAY],
+                         ids=["auto", "lane", "scan", "ray"])
 @pytest.mark.parametrize("depth", [10, 15])
 @pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
 def test_hair_patch_full_size_sampled(hair, flags, depth, variant):
