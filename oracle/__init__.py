@@ -85,6 +85,8 @@ def lib():
             L.orc_slab.argtypes = [vp, dbl, vp]; L.orc_slab.restype = i32
             L.orc_leaf_hit.argtypes = [vp, vp, i32, u32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.orc_leaf_hit.restype = i32
+            L.orc_normal.argtypes = [vp, vp, u32, u32, dbl, vp, ctypes.POINTER(dbl)]
+            L.orc_normal.restype = i32
             L.orc_limit_hit.argtypes = [vp, vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.orc_limit_hit.restype = i32
             L.orc_grad_t.argtypes = [vp, vp, dbl, dbl, vp]; L.orc_grad_t.restype = i32
@@ -242,6 +244,41 @@ def leaf_hit(ray, cp, depth, leaf):
     ok = lib().orc_leaf_hit(_p(_d(ray, (7,))), _p(_d(cp, (16,))), int(depth), int(leaf),
                             ctypes.byref(t), ctypes.byref(u))
     return (t.value, u.value) if ok else None
+
+
+def normal(ray, cp, start, size, t):
+    """Normal at a hit t on the leaf [start, start + size) (units of 2^-23)
+    of curve cp (App. C): (n (3,), kind, u) with kind 1 lateral, 2 / 3 the
+    end cap at u = 0 / 1."""
+    n = np.zeros(3)
+    u = ctypes.c_double()
+    k = lib().orc_normal(_p(_d(ray, 7)), _p(_d(cp, (4, 4))), int(start), int(size), float(t), _p(n),
+                         ctypes.byref(u))
+    return n, int(k), u.value
+
+
+def normals(case, depth, ref, pieces=None):
+    """Normals of the closest hits `ref` (from closest()) of a case: (n_ray, 3)
+    array, zero for misses, and the kind per ray (0 miss, 1 lateral, 2 / 3
+    end caps).  The leaf of a hit in a piece pre-split to level k has the size
+    2^-max(depth, k) of the segment."""
+    pieces = presplit(case["cps"]) if pieces is None else pieces
+    n_ray = len(ref["seg"])
+    out = np.zeros((n_ray, 3))
+    kind = np.zeros(n_ray, dtype=np.int32)
+    for i in np.nonzero(ref["seg"] >= 0)[0]:
+        s, leaf = int(ref["seg"][i]), int(ref["leaf"][i])
+        b, e = pieces["begin"][s], pieces["begin"][s + 1]
+        lvl = 0
+        for k in range(b, e):
+            lo = int(pieces["off"][k]) << (23 - int(pieces["level"][k]))
+            hi = (int(pieces["off"][k]) + 1) << (23 - int(pieces["level"][k]))
+            if lo <= leaf < hi:
+                lvl = int(pieces["level"][k])
+        size = ROOT_SIZE >> max(depth, lvl)
+        out[i], kind[i], _ = normal(ray7_from_packed(case["rays"][i]), case["cps"][s].astype(np.float64),
+                                    leaf, size, ref["t"][i])
+    return out, kind
 
 
 def limit_hit(ray, cp, n_grid=100000):

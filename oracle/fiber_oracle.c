@@ -737,6 +737,70 @@ int orc_leaf_hit(const double *ray7, const double *cp, int depth, uint32_t leaf,
     return 1;
 }
 
+/* ---------------------------------------------------------- hit normal */
+
+/*
+ * Normal at a hit (App. C, the routine that computes the intersection's u
+ * and normal).  The hit leaf [start, start + size) of the curve cp is
+ * rebuilt in the ray frame; the hit point (0, 0, t) is projected onto the
+ * leaf axis, u_local clamped to [0, 1], and u = u0 + u_local (u1 - u0).
+ *   - an end cap: the normal is p0 - p1, resp. p3 - p2, normalised (the
+ *     outward end-disk normal);
+ *   - otherwise the axis point a = p + u_local d and the normal is the hit
+ *     point minus a, taken back to world space (x e1 + y e2 + z w) and
+ *     normalised.
+ * (The listing's cur_c.axis and ray_direction are the leaf's d and the ray
+ * direction w; reading R9.)  The listing takes u == 0 or u == 1 for an end
+ * cap; a hit on an end disk projects onto the leaf axis a rounding away from
+ * either side of u_local = 0, so that test classifies end-disk hits by their
+ * rounding.  Reading R28: the hit is on the cap at u = 0 (u = 1) if its leaf
+ * is the first (last) one and the hit point lies on or beyond the segment's
+ * end plane through p0 with normal p1 - p0 (through p3, normal p3 - p2), to
+ * within 1e-12 (t + |p0|) here in FP64.  Writes n3 and returns 1 for a
+ * lateral normal, 2 for the cap at u = 0, 3 for the cap at u = 1; *u_out is
+ * the u above.
+ */
+int orc_normal(const double *ray7, const double *cp, uint32_t start, uint32_t size, double t,
+               double *n3, double *u_out)
+{
+    ray_t r = make_ray_d(ray7);
+    v4 Q[4];
+    node_t c;
+    to_ray_frame(&r, cp, Q);
+    if (start == 0 && size == ROOT_SIZE) node_of_points(Q, &c);
+    else node_at(Q, start, size, &c);
+    double dd = dot3(c.d, c.d), ul = 0.0;
+    if (dd > 0.0) {
+        v4 hb = V(-c.p.x, -c.p.y, t - c.p.z, 0.0);
+        ul = dmax(0.0, dmin(1.0, dot3(hb, c.d) / dd));
+    }
+    double u = (start + ul * size) * U_UNIT;
+    *u_out = u;
+    /* signed distances of the hit point beyond the two end planes */
+    v4 x = V(0.0, 0.0, t, 0.0);
+    v4 a0 = sub4(Q[0], Q[1]), a1 = sub4(Q[3], Q[2]);
+    double tol = 1e-12 * (t + sqrt(dot3(Q[0], Q[0])));
+    int cap0 = 0, cap1 = 0;
+    if (start == 0 && dot3(a0, a0) > 0.0) cap0 = dot3(sub4(x, Q[0]), a0) / sqrt(dot3(a0, a0)) >= -tol;
+    if (start + size == ROOT_SIZE && dot3(a1, a1) > 0.0)
+        cap1 = dot3(sub4(x, Q[3]), a1) / sqrt(dot3(a1, a1)) >= -tol;
+    double n[3];
+    int kind;
+    if (cap0 || cap1) {
+        int a = cap0 ? 0 : 3, b = cap0 ? 1 : 2;
+        for (int i = 0; i < 3; ++i) n[i] = cp[4 * a + i] - cp[4 * b + i];
+        kind = cap0 ? 2 : 3;
+    } else {
+        v4 ap = add4(c.p, mul4(ul, c.d));
+        double xx = -ap.x, yy = -ap.y, zz = t - ap.z;
+        for (int i = 0; i < 3; ++i) n[i] = xx * r.e1[i] + yy * r.e2[i] + zz * r.w[i];
+        kind = 1;
+    }
+    double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int i = 0; i < 3; ++i) n3[i] = len > 0.0 ? n[i] / len : 0.0;
+    return kind;
+}
+
 /* ---------------------------------------------------------- limit surface */
 
 /*

@@ -13,7 +13,7 @@ import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_primitives.py", "tests/test_oracle_traversal.py",
-        "tests/test_oracle_grad.py"]
+        "tests/test_oracle_grad.py", "tests/test_oracle_normals.py"]
 
 MUTATIONS = {
     "split_dp_coefficient": ("*dp = add4(add4(mul4(0.375, c->t0)", "*dp = add4(add4(mul4(0.125, c->t0)"),
@@ -40,6 +40,14 @@ MUTATIONS = {
                          "grad[4 * k + 3] = (a2 * (-2.0 * c.w * B[k]));"),
     "grad_dB": ("v4 g1 = sub4(mul4(dB[k], e), mul4(B[k], d1));", "v4 g1 = sub4(mul4(B[k], e), mul4(B[k], d1));"),
     "limit_G2_radius": ("*h = dot3(e, e) - c.w * c.w;", "*h = dot3(e, e) - c.w;"),
+    "normal_axis_point_sign": ("double xx = -ap.x, yy = -ap.y, zz = t - ap.z;",
+                               "double xx = ap.x, yy = -ap.y, zz = t - ap.z;"),
+    "normal_frame_swapped": ("n[i] = xx * r.e1[i] + yy * r.e2[i] + zz * r.w[i];",
+                             "n[i] = xx * r.e2[i] + yy * r.e1[i] + zz * r.w[i];"),
+    "normal_axis_point_unprojected": ("v4 ap = add4(c.p, mul4(ul, c.d));", "v4 ap = c.p;"),
+    "normal_cap_points": ("int a = cap0 ? 0 : 3, b = cap0 ? 1 : 2;", "int a = cap0 ? 0 : 3, b = cap0 ? 1 : 1;"),
+    "normal_cap_plane_sign": ("cap0 = dot3(sub4(x, Q[0]), a0) / sqrt(dot3(a0, a0)) >= -tol;",
+                              "cap0 = dot3(sub4(x, Q[0]), a0) / sqrt(dot3(a0, a0)) <= -tol;"),
 }
 
 
