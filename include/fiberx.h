@@ -198,6 +198,25 @@ fx_status intersect_backward(const fx_fibers *f, const float *rays, int64_t n_ra
                              float *grad_cps, unsigned long long *n_skipped_dev, void *stream);
 
 /*
+ * intersect_normals -- surface normals at the closest hits (App. C, the
+ * routine that computes the intersection's u and normal).
+ *
+ * Inputs: rays (as above), and tu, seg, leaf from intersect_closest on the
+ * same handle at the same depth (leaf is required).  Output: normal, n_ray x
+ * 3 floats, world space, unit length; (0, 0, 0) for misses.  The hit leaf is
+ * rebuilt in the ray frame and the hit point projected onto its axis; a
+ * lateral hit's normal is the hit point minus that axis point.  A hit on an
+ * end disk -- the first (last) leaf, hit point on or beyond the segment's end
+ * plane through p0 with normal p1 - p0 (through p3 with normal p3 - p2) to
+ * within 8 ulp of (t + |p0 - o|) -- gets the outward disk normal p0 - p1
+ * (p3 - p2).  flags: FX_FAST_MATH (approximate square root).
+ * Errors: FX_EINVAL (null pointers, negative size), FX_EDEPTH, FX_ECUDA.
+ */
+fx_status intersect_normals(const fx_fibers *f, const float *rays, int64_t n_ray, const float *tu,
+                            const int32_t *seg, const int32_t *leaf, int32_t depth, uint32_t flags,
+                            float *normal, void *stream);
+
+/*
  * intersect_closest_host -- intersect_closest on HOST buffers: copies rays,
  * row_ptr and seg_idx to device staging owned by the handle, runs, copies
  * tu / seg / leaf back and synchronises.  Host buffers should be pinned for

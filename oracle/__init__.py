@@ -85,7 +85,7 @@ def lib():
             L.orc_slab.argtypes = [vp, dbl, vp]; L.orc_slab.restype = i32
             L.orc_leaf_hit.argtypes = [vp, vp, i32, u32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.orc_leaf_hit.restype = i32
-            L.orc_normal.argtypes = [vp, vp, u32, u32, dbl, vp, ctypes.POINTER(dbl)]
+            L.orc_normal.argtypes = [vp, vp, u32, u32, dbl, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.orc_normal.restype = i32
             L.orc_limit_hit.argtypes = [vp, vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.orc_limit_hit.restype = i32
@@ -246,26 +246,30 @@ def leaf_hit(ray, cp, depth, leaf):
     return (t.value, u.value) if ok else None
 
 
-def normal(ray, cp, start, size, t):
+def normal(ray, cp, start, size, t, with_len=False):
     """Normal at a hit t on the leaf [start, start + size) (units of 2^-23)
     of curve cp (App. C): (n (3,), kind, u) with kind 1 lateral, 2 / 3 the
-    end cap at u = 0 / 1."""
+    end cap at u = 0 / 1; with_len adds the vector's length before it was
+    normalised."""
     n = np.zeros(3)
     u = ctypes.c_double()
+    ln = ctypes.c_double()
     k = lib().orc_normal(_p(_d(ray, 7)), _p(_d(cp, (4, 4))), int(start), int(size), float(t), _p(n),
-                         ctypes.byref(u))
-    return n, int(k), u.value
+                         ctypes.byref(u), ctypes.byref(ln))
+    return (n, int(k), u.value, ln.value) if with_len else (n, int(k), u.value)
 
 
 def normals(case, depth, ref, pieces=None):
     """Normals of the closest hits `ref` (from closest()) of a case: (n_ray, 3)
-    array, zero for misses, and the kind per ray (0 miss, 1 lateral, 2 / 3
-    end caps).  The leaf of a hit in a piece pre-split to level k has the size
-    2^-max(depth, k) of the segment."""
+    array (zero for misses), the kind per ray (0 miss, 1 lateral, 2 / 3 end
+    caps) and the length of each normal before it was normalised.  The leaf of
+    a hit in a piece pre-split to level k has the size 2^-max(depth, k) of
+    the segment."""
     pieces = presplit(case["cps"]) if pieces is None else pieces
     n_ray = len(ref["seg"])
     out = np.zeros((n_ray, 3))
     kind = np.zeros(n_ray, dtype=np.int32)
+    length = np.zeros(n_ray)
     for i in np.nonzero(ref["seg"] >= 0)[0]:
         s, leaf = int(ref["seg"][i]), int(ref["leaf"][i])
         b, e = pieces["begin"][s], pieces["begin"][s + 1]
@@ -276,9 +280,10 @@ def normals(case, depth, ref, pieces=None):
             if lo <= leaf < hi:
                 lvl = int(pieces["level"][k])
         size = ROOT_SIZE >> max(depth, lvl)
-        out[i], kind[i], _ = normal(ray7_from_packed(case["rays"][i]), case["cps"][s].astype(np.float64),
-                                    leaf, size, ref["t"][i])
-    return out, kind
+        out[i], kind[i], _, length[i] = normal(ray7_from_packed(case["rays"][i]),
+                                               case["cps"][s].astype(np.float64), leaf, size, ref["t"][i],
+                                               with_len=True)
+    return out, kind, length
 
 
 def limit_hit(ray, cp, n_grid=100000):

@@ -758,10 +758,12 @@ int orc_leaf_hit(const double *ray7, const double *cp, int depth, uint32_t leaf,
  * end plane through p0 with normal p1 - p0 (through p3, normal p3 - p2), to
  * within 1e-12 (t + |p0|) here in FP64.  Writes n3 and returns 1 for a
  * lateral normal, 2 for the cap at u = 0, 3 for the cap at u = 1; *u_out is
- * the u above.
+ * the u above and *len_out (if not null) the length of the vector before it
+ * was normalised (for a lateral hit, the hit point's distance from the axis
+ * point).
  */
 int orc_normal(const double *ray7, const double *cp, uint32_t start, uint32_t size, double t,
-               double *n3, double *u_out)
+               double *n3, double *u_out, double *len_out)
 {
     ray_t r = make_ray_d(ray7);
     v4 Q[4];
@@ -798,6 +800,7 @@ int orc_normal(const double *ray7, const double *cp, uint32_t start, uint32_t si
     }
     double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     for (int i = 0; i < 3; ++i) n3[i] = len > 0.0 ? n[i] / len : 0.0;
+    if (len_out) *len_out = len;
     return kind;
 }
 

@@ -367,6 +367,22 @@ fx_status intersect_backward(const fx_fibers* f, const float* rays, int64_t n_ra
   return FX_OK;
 }
 
+fx_status intersect_normals(const fx_fibers* f, const float* rays, int64_t n_ray, const float* tu,
+                            const int32_t* seg, const int32_t* leaf, int32_t depth, uint32_t flags,
+                            float* normal, void* stream) {
+  if (!f) return fail(FX_EINVAL, "null fiber handle");
+  if (n_ray < 0 || n_ray > 0x7fffffffLL) return fail(FX_EINVAL, "n_ray out of range");
+  if (depth < 0 || depth > fx::kMaxDepth) return fail(FX_EDEPTH, "depth outside [0, 23]");
+  if (n_ray == 0) return FX_OK;
+  if (!rays || !tu || !seg || !leaf || !normal) return fail(FX_EINVAL, "null argument");
+  fx::TraceArgs a = make_args(f, rays, n_ray, nullptr, nullptr, 0, depth);
+  a.tu = reinterpret_cast<float2*>(const_cast<float*>(tu));
+  a.seg = const_cast<int32_t*>(seg);
+  a.leaf = const_cast<int32_t*>(leaf);
+  FX_CUDA(fx::launch_normals(a, f->seg_cp, normal, flags, (cudaStream_t)stream));
+  return FX_OK;
+}
+
 fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
                                  const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags,
                                  float* tu, int32_t* seg, int32_t* leaf, void* stream) {

@@ -107,6 +107,10 @@ cudaError_t launch_ray(const TraceArgs &a, bool pairs, uint32_t flags, cudaStrea
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,
                             int sm_count, cudaStream_t s);
 
+// normal_kernels.cu: hit normals from closest-hit results (App. C)
+cudaError_t launch_normals(const TraceArgs &a, const float4 *seg_cp, float *normal, uint32_t flags,
+                           cudaStream_t s);
+
 // peak.cu: FP32 FMA microbenchmark (synchronises s); flops = FMA flops of the
 // timed launch
 cudaError_t fma_peak(int sm_count, int blocks_per_sm, int iters, float *ms, double *flops, cudaStream_t s);

@@ -39,7 +39,8 @@ FX_VARIANT_RAY = 5
 
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
-           "intersect_backward", "intersect_closest_host", "intersect_closest_noalloc", "fx_set_launch",
+           "intersect_backward", "intersect_normals", "intersect_closest_host", "intersect_closest_noalloc",
+           "fx_set_launch",
            "fx_get_launch", "fx_counters", "fx_stream_status", "fx_fma_peak", "fx_last_error", "fx_version"]
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -97,6 +98,8 @@ def lib():
             L.intersect_pairs.restype = i32
             L.intersect_backward.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
             L.intersect_backward.restype = i32
+            L.intersect_normals.argtypes = [vp, vp, i64, vp, vp, vp, i32, u32, vp, vp]
+            L.intersect_normals.restype = i32
             L.intersect_closest_host.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
             L.intersect_closest_host.restype = i32
             L.intersect_closest_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
@@ -278,6 +281,21 @@ def intersect_pairs(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, s
     _check(lib().intersect_pairs(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx), n_pair,
                                  int(depth), int(flags), _ptr(tu), _ptr(lf), _stream(stream)))
     return tu, lf
+
+
+def intersect_normals(fibers, rays, tu, seg, leaf, depth, flags=0, stream=None, out=None):
+    """Unit surface normals [n_ray, 3] at the closest hits (tu, seg, leaf from
+    intersect_closest at `depth`); zero for misses."""
+    import torch
+    dev = fibers.device
+    rays = _dev(rays, torch.float32, dev)
+    tu = _dev(tu, torch.float32, dev)
+    seg = _dev(seg, torch.int32, dev)
+    leaf = _dev(leaf, torch.int32, dev)
+    n = out if out is not None else torch.empty((rays.shape[0], 3), dtype=torch.float32, device=dev)
+    _check(lib().intersect_normals(fibers.handle, _ptr(rays), rays.shape[0], _ptr(tu), _ptr(seg), _ptr(leaf),
+                                   int(depth), int(flags), _ptr(n), _stream(stream)))
+    return n
 
 
 def intersect_backward(fibers, rays, tu, seg, grad_t, grad_cps=None, stream=None):
