@@ -130,6 +130,27 @@ typedef struct {
 fx_status fiber_upload(const float *cps, int64_t n_seg, int32_t cps_on_device,
                        const fx_upload_opts *opts, void *stream, fx_fibers **out);
 
+/*
+ * fiber_upload_quadratic -- fiber_upload for quadratic Bezier segments (the
+ * paper evaluates quadratic and cubic fibers, Sec. 4; their constraint is
+ * App. B.1's <p1 - p0, p1 - p2> <= 0).
+ *
+ * cps: n_seg x 3 control points x (x, y, z, r) floats, r >= 0; host or device
+ * memory as cps_on_device says; copied.  Each segment is raised to the cubic
+ * with the same curve and parametrisation (degree elevation, in FP64, all
+ * four components: q0 = p0, q1 = (p0 + 2 p1) / 3, q2 = (2 p1 + p2) / 3,
+ * q3 = p2) and then uploaded as fiber_upload does, so every intersect_* call
+ * and its u, leaf and segment ids refer to the quadratic segment.  A
+ * quadratic that meets App. B.1's constraint raises to a cubic that meets the
+ * five cubic constraints of Sec. 3.4, so it is not pre-split.  The handle's
+ * control points for intersect_backward are the raised cubic's: grad_cps is
+ * n_seg x 4 x 4, with respect to q0..q3 (the chain rule to p0..p2 is
+ * dq0/dp0 = 1, dq1/dp0 = 1/3, dq1/dp1 = 2/3, dq2/dp1 = 2/3, dq2/dp2 = 1/3,
+ * dq3/dp2 = 1).  Errors as fiber_upload.
+ */
+fx_status fiber_upload_quadratic(const float *cps, int64_t n_seg, int32_t cps_on_device,
+                                 const fx_upload_opts *opts, void *stream, fx_fibers **out);
+
 /* Releases the handle and its device memory (NULL is a no-op). */
 void fiber_free(fx_fibers *f);
 

@@ -67,6 +67,10 @@ def lib():
             L.orc_valid_cubic.argtypes = [vp]; L.orc_valid_cubic.restype = i32
             L.orc_thick_ok.argtypes = [vp]; L.orc_thick_ok.restype = i32
             L.orc_split_half.argtypes = [vp, vp, vp]; L.orc_split_half.restype = None
+            L.orc_presplit_d.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp, i64]
+            L.orc_presplit_d.restype = i64
+            L.orc_valid_quadratic.argtypes = [vp]; L.orc_valid_quadratic.restype = i32
+            L.orc_elevate_quadratic.argtypes = [vp, vp]; L.orc_elevate_quadratic.restype = None
             L.orc_presplit.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp, i64]
             L.orc_presplit.restype = i64
             L.orc_intersect.argtypes = [vp, vp, i32, ctypes.POINTER(OrcHit)]
@@ -115,6 +119,22 @@ def ray7_from_packed(r8):
 
 # ----------------------------------------------------------------- wrappers
 
+def valid_quadratic(cp):
+    """App. B.1's constraint on a quadratic curve [3, 4]."""
+    return bool(lib().orc_valid_quadratic(_p(_d(cp, (12,)))))
+
+
+def elevate_quadratics(cps):
+    """[n, 3, 4] quadratic control points -> [n, 4, 4] float64 cubic ones with
+    the same curve and parametrisation."""
+    q = np.ascontiguousarray(cps, dtype=np.float64).reshape(-1, 12)
+    out = np.zeros((q.shape[0], 16))
+    L = lib()
+    for i in range(q.shape[0]):
+        L.orc_elevate_quadratic(q[i].ctypes.data_as(ctypes.c_void_p), out[i].ctypes.data_as(ctypes.c_void_p))
+    return out.reshape(-1, 4, 4)
+
+
 def valid_cubic(cp):
     return bool(lib().orc_valid_cubic(_p(_d(cp, (16,)))))
 
@@ -132,14 +152,24 @@ def split_half(cp):
 
 def presplit(cps, max_level=MAX_PRESPLIT, thick=True):
     """Pieces of every segment: dict(cp [n,4,4] f64, seg, level, off, flags,
-    begin [n_seg+1])."""
-    cps = np.ascontiguousarray(cps, dtype=np.float32).reshape(-1, 16)
-    n_seg = cps.shape[0]
+    begin [n_seg+1]).  Cubic control points [n,4,4] (float32 as given, or
+    float64 kept in double precision), or quadratic ones [n,3,4], which are
+    raised to cubics in FP64 first."""
+    cps = np.asarray(cps)
+    if cps.ndim == 3 and cps.shape[1] == 3:
+        cps = elevate_quadratics(cps)
     L = lib()
-    n = L.orc_presplit(_p(cps), n_seg, max_level, int(thick), None, None, None, None, None, 0)
+    if cps.dtype == np.float64:
+        cps = np.ascontiguousarray(cps).reshape(-1, 16)
+        split = L.orc_presplit_d
+    else:
+        cps = np.ascontiguousarray(cps, dtype=np.float32).reshape(-1, 16)
+        split = L.orc_presplit
+    n_seg = cps.shape[0]
+    n = split(_p(cps), n_seg, max_level, int(thick), None, None, None, None, None, 0)
     cp = np.zeros((max(n, 1), 16)); seg = np.zeros(max(n, 1), np.int32)
     lv = np.zeros_like(seg); off = np.zeros_like(seg); fl = np.zeros_like(seg)
-    L.orc_presplit(_p(cps), n_seg, max_level, int(thick), _p(cp), _p(seg), _p(lv), _p(off), _p(fl), n)
+    split(_p(cps), n_seg, max_level, int(thick), _p(cp), _p(seg), _p(lv), _p(off), _p(fl), n)
     begin = np.zeros(n_seg + 1, np.int32)
     np.add.at(begin, seg[:n] + 1, 1)
     begin = np.cumsum(begin).astype(np.int32)

@@ -498,6 +498,51 @@ int64_t orc_presplit(const float *cps, int64_t n_seg, int max_level, int thick, 
     return o.n;
 }
 
+/* The same for control points given in double precision. */
+int64_t orc_presplit_d(const double *cps, int64_t n_seg, int max_level, int thick, double *piece_cp,
+                       int32_t *piece_seg, int32_t *piece_level, int32_t *piece_off,
+                       int32_t *piece_flags, int64_t cap)
+{
+    piece_out o = {piece_cp, piece_seg, piece_level, piece_off, piece_flags, 0, cap};
+    for (int64_t s = 0; s < n_seg; ++s)
+        presplit_rec(cps + 16 * s, (int32_t)s, 0, 0, max_level, thick, &o);
+    return o.n;
+}
+
+/* ------------------------------------------------------ quadratic curves */
+
+/*
+ * App. B.1: a quadratic curve (p0, p1, p2) can be split recursively at the
+ * domain centre into subcurves with disjoint bounding volumes when
+ * <p1 - p0, p1 - p2> <= 0 (positions).  (The lemma states "if and only if",
+ * but its two one-sided conditions <p1 - p0, p2 - p0> >= 0 and
+ * <p1 - p2, p0 - p2> >= 0 do not imply the combined one; the combined one is
+ * the one its second lemma carries to every subcurve.  Reading R29.)
+ */
+int orc_valid_quadratic(const double *cp12)
+{
+    v4 a = sub4(load_cp(cp12, 1), load_cp(cp12, 0)), b = sub4(load_cp(cp12, 1), load_cp(cp12, 2));
+    return dot3(a, b) <= 0.0;
+}
+
+/*
+ * Degree elevation of a quadratic Bezier curve to the cubic with the same
+ * curve and parametrisation (all four components, radius included):
+ * q0 = p0, q1 = (p0 + 2 p1) / 3, q2 = (2 p1 + p2) / 3, q3 = p2.  The method's
+ * representation and subdivision rules (Sec. 3.1) are stated for cubics; a
+ * quadratic fiber is intersected as its raised cubic (reading R29).
+ */
+void orc_elevate_quadratic(const double *cp12, double *cp16)
+{
+    for (int a = 0; a < 4; ++a) {
+        double p0 = cp12[a], p1 = cp12[4 + a], p2 = cp12[8 + a];
+        cp16[a] = p0;
+        cp16[4 + a] = (p0 + 2.0 * p1) / 3.0;
+        cp16[8 + a] = (2.0 * p1 + p2) / 3.0;
+        cp16[12 + a] = p2;
+    }
+}
+
 /* ------------------------------------------------------ exported entries */
 
 /* One ray (7 doubles: o, w, t_max) against one curve at the given depth. */

@@ -139,65 +139,41 @@ bool device_is_sm103(int dev, int* sm_count) {
   return p.major == 10 && p.minor == 3;
 }
 
-}  // namespace
-
-namespace fx {
-void set_last_error(const std::string& msg) { g_err = msg; }
-}  // namespace fx
-
-extern "C" {
-
-const char* fx_last_error(void) { return g_err.c_str(); }
-
-fx_status fx_fma_peak(int32_t blocks_per_sm, int32_t iters, float* ms, double* tflops, void* stream) {
-  if (!ms || !tflops) return fail(FX_EINVAL, "null output");
-  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1) return fail(FX_EINVAL, "blocks_per_sm or iters out of range");
-  int dev = 0, sms = 0;
-  FX_CUDA(cudaGetDevice(&dev));
-  FX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  double flops = 0.0;
-  FX_CUDA(fx::fma_peak(sms, blocks_per_sm, iters, ms, &flops, (cudaStream_t)stream));
-  *tflops = flops / (*ms * 1e-3) / 1e12;
-  return FX_OK;
-}
-
-int32_t fx_version(void) { return 10000; }
-
-fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, const fx_upload_opts* opts,
-                       void* stream, fx_fibers** out) {
-  if (!out) return fail(FX_EINVAL, "null output handle");
-  *out = nullptr;
-  if (n_seg < 0 || n_seg > 0x7ffffffeLL) return fail(FX_EINVAL, "n_seg out of range");
-  if (n_seg > 0 && !cps) return fail(FX_EINVAL, "null control points");
-  const int max_presplit = opts ? opts->max_presplit : 8;
-  const bool thick = opts ? opts->thick_check != 0 : true;
-  if (max_presplit < 0 || max_presplit > 8) return fail(FX_EINVAL, "max_presplit outside [0, 8]");
-  cudaStream_t s = (cudaStream_t)stream;
-
-  int dev = 0, sms = 0;
-  FX_CUDA(cudaGetDevice(&dev));
-  if (!device_is_sm103(dev, &sms)) return fail(FX_EDEVICE, "current device is not sm_103");
-
-  std::vector<float> host((size_t)n_seg * 16);
+// Reads n_seg x n_cp x 4 floats from host or device memory and checks them:
+// finite, radius >= 0.
+fx_status read_cps(const float* cps, int64_t n_seg, int n_cp, int32_t on_device, cudaStream_t s,
+                   std::vector<float>& host) {
+  host.resize((size_t)n_seg * n_cp * 4);
   if (n_seg > 0) {
-    if (cps_on_device) {
+    if (on_device) {
       FX_CUDA(cudaMemcpyAsync(host.data(), cps, host.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
       FX_CUDA(cudaStreamSynchronize(s));
     } else {
       std::memcpy(host.data(), cps, host.size() * sizeof(float));
     }
   }
-  for (int64_t i = 0; i < n_seg; ++i) {
-    for (int k = 0; k < 16; ++k)
-      if (!std::isfinite(host[16 * i + k])) return fail(FX_EINVAL, "non-finite control point");
-    for (int k = 0; k < 4; ++k)
-      if (host[16 * i + 4 * k + 3] < 0.0f) return fail(FX_EINVAL, "negative radius");
+  for (size_t i = 0; i < host.size(); ++i) {
+    if (!std::isfinite(host[i])) return fail(FX_EINVAL, "non-finite control point");
+    if (i % 4 == 3 && host[i] < 0.0f) return fail(FX_EINVAL, "negative radius");
   }
+  return FX_OK;
+}
+
+// Upload of cubic segments given in double precision (n_seg x 16); `host` is
+// the FP32 copy kept on the device for the polish, adjoint and normals.
+fx_status upload_cubics(const std::vector<double>& cps64, const std::vector<float>& host, int64_t n_seg,
+                        const fx_upload_opts* opts, cudaStream_t s, fx_fibers** out) {
+  const int max_presplit = opts ? opts->max_presplit : 8;
+  const bool thick = opts ? opts->thick_check != 0 : true;
+  if (max_presplit < 0 || max_presplit > 8) return fail(FX_EINVAL, "max_presplit outside [0, 8]");
+  int dev = 0, sms = 0;
+  FX_CUDA(cudaGetDevice(&dev));
+  if (!device_is_sm103(dev, &sms)) return fail(FX_EDEVICE, "current device is not sm_103");
 
   std::vector<fx::PieceRec> pieces;
   std::vector<int32_t> begin;
   const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-  fx::presplit_all(host.data(), n_seg, max_presplit, thick, n_seg > 4096 ? nt : 1, pieces, begin);
+  fx::presplit_all(cps64.data(), n_seg, max_presplit, thick, n_seg > 4096 ? nt : 1, pieces, begin);
 
   fx_fibers* f = new (std::nothrow) fx_fibers();
   if (!f) return fail(FX_ENOMEM, "handle allocation");
@@ -273,6 +249,74 @@ fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, c
   *out = f;
   return FX_OK;
 }
+
+}  // namespace
+
+namespace fx {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace fx
+
+extern "C" {
+
+const char* fx_last_error(void) { return g_err.c_str(); }
+
+fx_status fx_fma_peak(int32_t blocks_per_sm, int32_t iters, float* ms, double* tflops, void* stream) {
+  if (!ms || !tflops) return fail(FX_EINVAL, "null output");
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1) return fail(FX_EINVAL, "blocks_per_sm or iters out of range");
+  int dev = 0, sms = 0;
+  FX_CUDA(cudaGetDevice(&dev));
+  FX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double flops = 0.0;
+  FX_CUDA(fx::fma_peak(sms, blocks_per_sm, iters, ms, &flops, (cudaStream_t)stream));
+  *tflops = flops / (*ms * 1e-3) / 1e12;
+  return FX_OK;
+}
+
+int32_t fx_version(void) { return 10000; }
+
+fx_status fiber_upload(const float* cps, int64_t n_seg, int32_t cps_on_device, const fx_upload_opts* opts,
+                       void* stream, fx_fibers** out) {
+  if (!out) return fail(FX_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n_seg < 0 || n_seg > 0x7ffffffeLL) return fail(FX_EINVAL, "n_seg out of range");
+  if (n_seg > 0 && !cps) return fail(FX_EINVAL, "null control points");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<float> host;
+  fx_status st = read_cps(cps, n_seg, 4, cps_on_device, s, host);
+  if (st != FX_OK) return st;
+  std::vector<double> cps64(host.begin(), host.end());
+  return upload_cubics(cps64, host, n_seg, opts, s, out);
+}
+
+fx_status fiber_upload_quadratic(const float* cps, int64_t n_seg, int32_t cps_on_device,
+                                 const fx_upload_opts* opts, void* stream, fx_fibers** out) {
+  if (!out) return fail(FX_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n_seg < 0 || n_seg > 0x7ffffffeLL) return fail(FX_EINVAL, "n_seg out of range");
+  if (n_seg > 0 && !cps) return fail(FX_EINVAL, "null control points");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<float> host;
+  fx_status st = read_cps(cps, n_seg, 3, cps_on_device, s, host);
+  if (st != FX_OK) return st;
+  // exact degree elevation (all four components): q0 = p0, q1 = (p0 + 2 p1) / 3,
+  // q2 = (2 p1 + p2) / 3, q3 = p2 -- the same curve and parametrisation
+  std::vector<double> cps64((size_t)n_seg * 16);
+  std::vector<float> cps32((size_t)n_seg * 16);
+  for (int64_t i = 0; i < n_seg; ++i) {
+    const float* q = &host[12 * i];
+    double* c = &cps64[16 * i];
+    for (int a = 0; a < 4; ++a) {
+      const double p0 = q[a], p1 = q[4 + a], p2 = q[8 + a];
+      c[a] = p0;
+      c[4 + a] = (p0 + 2.0 * p1) / 3.0;
+      c[8 + a] = (2.0 * p1 + p2) / 3.0;
+      c[12 + a] = p2;
+    }
+    for (int k = 0; k < 16; ++k) cps32[16 * i + k] = (float)c[k];
+  }
+  return upload_cubics(cps64, cps32, n_seg, opts, s, out);
+}
+
 
 void fiber_free(fx_fibers* f) {
   if (!f) return;

@@ -198,7 +198,7 @@ void split_rec(const Curve& c, int level, int off, int max_level, bool thick,
 
 }  // namespace
 
-void presplit_all(const float* cps, int64_t n_seg, int max_level, bool thick, int n_threads,
+void presplit_all(const double* cps, int64_t n_seg, int max_level, bool thick, int n_threads,
                   std::vector<PieceRec>& pieces, std::vector<int32_t>& begin) {
   if (n_threads < 1) n_threads = 1;
   const int64_t per = (n_seg + n_threads - 1) / std::max(1, n_threads);

@@ -18,7 +18,8 @@ struct PieceRec {
 
 // Pieces of all segments in segment order; begin[s] .. begin[s + 1] are the
 // pieces of segment s (begin has n_seg + 1 entries).
-void presplit_all(const float* cps, int64_t n_seg, int max_level, bool thick, int n_threads,
+// cps: n_seg x 4 control points x (x, y, z, r), in double precision.
+void presplit_all(const double* cps, int64_t n_seg, int max_level, bool thick, int n_threads,
                   std::vector<PieceRec>& pieces, std::vector<int32_t>& begin);
 
 }  // namespace fx

@@ -38,7 +38,7 @@ FX_VARIANT_SCAN = 4
 FX_VARIANT_RAY = 5
 
 MAX_DEPTH = 23
-EXPORTS = ["fiber_upload", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
+EXPORTS = ["fiber_upload", "fiber_upload_quadratic", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
            "intersect_backward", "intersect_normals", "intersect_closest_host", "intersect_closest_noalloc",
            "fx_set_launch",
            "fx_get_launch", "fx_counters", "fx_stream_status", "fx_fma_peak", "fx_last_error", "fx_version"]
@@ -88,6 +88,8 @@ def lib():
             vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
             L.fiber_upload.argtypes = [vp, i64, i32, ctypes.POINTER(UploadOpts), vp, ctypes.POINTER(vp)]
             L.fiber_upload.restype = i32
+            L.fiber_upload_quadratic.argtypes = [vp, i64, i32, ctypes.POINTER(UploadOpts), vp, ctypes.POINTER(vp)]
+            L.fiber_upload_quadratic.restype = i32
             L.fiber_free.argtypes = [vp]
             L.fiber_free.restype = None
             L.fiber_info.argtypes = [vp, ctypes.POINTER(FibersInfo)]
@@ -147,7 +149,9 @@ def _dev(x, dtype, device):
 
 class Fibers:
     """Device copy of fiber segments (fiber_upload).  ``cps``: [n_seg, 4, 4]
-    float32 (x, y, z, r per control point), host or device."""
+    float32 (x, y, z, r per control point) for cubic segments, or
+    [n_seg, 3, 4] for quadratic ones (fiber_upload_quadratic), host or
+    device."""
 
     def __init__(self, cps, max_presplit=8, thick_check=True, stream=None, device=None):
         import torch
@@ -155,16 +159,18 @@ class Fibers:
         if isinstance(cps, np.ndarray):
             cps = torch.from_numpy(np.ascontiguousarray(cps, dtype=np.float32))
         cps = cps.detach().to(torch.float32).contiguous()
-        if cps.dim() != 3 or cps.shape[1:] != (4, 4):
-            raise ValueError("cps must be [n_seg, 4, 4]")
+        if cps.dim() != 3 or cps.shape[1:] not in ((4, 4), (3, 4)):
+            raise ValueError("cps must be [n_seg, 4, 4] (cubic) or [n_seg, 3, 4] (quadratic)")
+        self.quadratic = cps.shape[1] == 3
+        upload = L.fiber_upload_quadratic if self.quadratic else L.fiber_upload
         self.device = torch.device(device) if device is not None else (
             cps.device if cps.is_cuda else torch.device("cuda", torch.cuda.current_device()))
         self.n_seg = int(cps.shape[0])
         opts = UploadOpts(int(max_presplit), int(bool(thick_check)))
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(L.fiber_upload(_ptr(cps) if cps.numel() else None, self.n_seg, int(cps.is_cuda),
-                                  ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+            _check(upload(_ptr(cps) if cps.numel() else None, self.n_seg, int(cps.is_cuda),
+                          ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
         self._h = h
         self._lib = L
 
