@@ -369,6 +369,11 @@ def _autograd():
             if grad_t is None:
                 return (None,) * 7
             g, _ = intersect_backward(ctx.fibers, rays, tu, seg, grad_t.float().contiguous())
+            if ctx.fibers.quadratic:
+                # the adjoint is with respect to the raised cubic q0..q3; the
+                # chain rule through q1 = (p0 + 2 p1) / 3, q2 = (2 p1 + p2) / 3
+                g = torch.stack([g[:, 0] + g[:, 1] / 3.0, (2.0 / 3.0) * (g[:, 1] + g[:, 2]),
+                                 g[:, 2] / 3.0 + g[:, 3]], dim=1)
             return g.reshape(ctx.cps_shape), None, None, None, None, None, None
 
     return FiberIntersect

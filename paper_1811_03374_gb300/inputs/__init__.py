@@ -343,6 +343,48 @@ def single_fiber_case(klass: str, n_ray: int, seed: int = SEED_BASE + 5):
     return dict(cps=cps, rays=rays, row_ptr=row_ptr, seg_idx=seg_idx, name="single_%s" % klass)
 
 
+def quadratic_segments(g, n, jitter, L=1.0):
+    """Quadratic segments [n, 3, 4]: p0 ~ U[-10, 10]^3, p2 = p0 + L u (u
+    uniform on the sphere), p1 = the chord's midpoint + jitter * L * (a point
+    of the unit ball), radius U[0.001, 0.01] L per control point."""
+    p0 = g.uniform(-10.0, 10.0, (n, 3))
+    p2 = p0 + L * _unit_sphere(g, n)
+    p1 = 0.5 * (p0 + p2) + jitter * L * _unit_ball(g, n)
+    r = g.uniform(0.001, 0.01, (n, 3)) * L
+    cps = np.stack([p0, p1, p2], axis=1)
+    return np.concatenate([cps, r[..., None]], axis=-1).astype(np.float32)
+
+
+def quadratic_eval(cps, u):
+    """Quadratic Bezier point (all four components) by de Casteljau, for
+    aiming rays."""
+    u = np.asarray(u)[:, None]
+    a = (1 - u) * cps[:, 0] + u * cps[:, 1]
+    b = (1 - u) * cps[:, 1] + u * cps[:, 2]
+    return (1 - u) * a + u * b
+
+
+def quadratic_case(klass: str, n: int, seed: int = SEED_BASE + 6, forced_hits: bool = False):
+    """The depth-sweep workload for quadratic fibers: one ray per segment,
+    aimed at its radius-dilated control-hull box, or (forced_hits) at
+    c(u) + delta with |delta| < r(u)."""
+    g = rng(seed + 7919 * list(SWEEP_JITTER).index(klass))
+    cps = quadratic_segments(g, n, SWEEP_JITTER[klass])
+    c64 = cps.astype(np.float64)
+    if forced_hits:
+        c = quadratic_eval(c64, g.uniform(0.0, 1.0, n))
+        target = c[:, :3] + 0.9 * c[:, 3:4] * _unit_ball(g, n)
+    else:
+        rmax = c64[:, :, 3].max(axis=1, keepdims=True)
+        lo = c64[:, :, :3].min(axis=1) - rmax
+        hi = c64[:, :, :3].max(axis=1) + rmax
+        target = lo + (hi - lo) * g.uniform(0.0, 1.0, (n, 3))
+    w = _unit_sphere(g, n)
+    rays = pack_rays(target - 10.0 * w, w)
+    row_ptr, seg_idx = diagonal_csr(n)
+    return dict(cps=cps, rays=rays, row_ptr=row_ptr, seg_idx=seg_idx, name="quadratic_%s" % klass)
+
+
 # --------------------------------------------------------------------------
 # workload 3: precision stress
 # --------------------------------------------------------------------------

@@ -71,3 +71,11 @@ def test_single_fiber_case():
         assert np.all(c["seg_idx"] == 0) and c["row_ptr"][-1] == 1000
         w = c["rays"][:, 4:7].astype(np.float64)
         np.testing.assert_allclose(np.linalg.norm(w, axis=1), 1.0, rtol=1e-6)
+
+
+def test_quadratic_case():
+    for k in I.SWEEP_JITTER:
+        c = I.quadratic_case(k, 500, forced_hits=True)
+        assert c["cps"].shape == (500, 3, 4) and c["rays"].shape == (500, 8)
+        L = np.linalg.norm(c["cps"][:, 2, :3].astype(np.float64) - c["cps"][:, 0, :3], axis=1)
+        np.testing.assert_allclose(L, 1.0, rtol=1e-5)
