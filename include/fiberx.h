@@ -62,6 +62,7 @@ typedef enum {
 #define FX_POLISH_FP64 0x4u       /* re-evaluate each hit's leaf and its neighbours in FP64, keep the nearest (intersect_closest) */
 #define FX_COUNT 0x8u             /* accumulate node / descent / backtrack counters */
 #define FX_CHECK_INDEX 0x10u      /* range-check candidate segment ids on the device */
+#define FX_COUNT_BOXES 0x20u      /* intersect_counts: ray-frame axis-aligned boxes instead of cylinders */
 
 typedef struct fx_fibers fx_fibers; /* opaque; owns the device copy of the fibers */
 
@@ -236,6 +237,29 @@ fx_status intersect_backward(const fx_fibers *f, const float *rays, int64_t n_ra
 fx_status intersect_normals(const fx_fibers *f, const float *rays, int64_t n_ray, const float *tu,
                             const int32_t *seg, const int32_t *leaf, int32_t depth, uint32_t flags,
                             float *normal, void *stream);
+
+/*
+ * intersect_counts -- per-ray pruning-test counts, the statistic of Fig. 8
+ * (oriented bounding cylinders against axis-aligned boxes).
+ *
+ * Same inputs as intersect_closest.  Each ray's candidates are searched in
+ * row order with the closest hit so far as t_max, with no test before the
+ * root's, so only the bounding volume differs:
+ *   - default: the traversal of Sec. 3.3; one count per node tested;
+ *   - FX_COUNT_BOXES: the same subdivision without partition planes, each
+ *     node bounded by the box [min_k (q_k - r_k), max_k (q_k + r_k)] of its
+ *     control points q_k and radii r_k in the ray's frame.  Both children of
+ *     a hit node are tested (two counts), the one with the smaller z_min is
+ *     searched first and the other tested again (one count) when taken up;
+ *     the search does not end at the first leaf hit.
+ * Output: counts, n_ray uint32 (saturating).  flags: FX_FAST_MATH,
+ * FX_CHECK_INDEX, FX_COUNT_BOXES.  Handles whose segments are single level-0
+ * pieces only (FX_EUNSUPPORTED otherwise).  Errors: FX_EINVAL, FX_EDEPTH,
+ * FX_EUNSUPPORTED, FX_ECUDA.
+ */
+fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray, const int32_t *row_ptr,
+                           const int32_t *seg_idx, int64_t n_pair, int32_t depth, uint32_t flags,
+                           uint32_t *counts, void *stream);
 
 /*
  * intersect_closest_host -- intersect_closest on HOST buffers: copies rays,

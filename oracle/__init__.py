@@ -67,6 +67,8 @@ def lib():
             L.orc_valid_cubic.argtypes = [vp]; L.orc_valid_cubic.restype = i32
             L.orc_thick_ok.argtypes = [vp]; L.orc_thick_ok.restype = i32
             L.orc_split_half.argtypes = [vp, vp, vp]; L.orc_split_half.restype = None
+            L.orc_ray_counts.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp]
+            L.orc_ray_counts.restype = None
             L.orc_presplit_d.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp, i64]
             L.orc_presplit_d.restype = i64
             L.orc_valid_quadratic.argtypes = [vp]; L.orc_valid_quadratic.restype = i32
@@ -205,6 +207,22 @@ def closest(case, depth, pieces=None, nthreads=0):
                       _p(cnt))
     return dict(t=t, u=u, seg=seg, leaf=leaf,
                 counters=dict(zip(["nodes", "descents", "backtracks", "hits", "tests"], cnt.tolist())))
+
+
+def ray_counts(case, depth, mode, pieces=None, nthreads=0):
+    """Per-ray pruning tests (Fig. 8; reading R30): mode "cylinder" (the
+    traversal's node tests) or "box" (ray-frame axis-aligned boxes); each ray's
+    candidates in row order with the closest hit so far as t_max.  Returns
+    (counts int64 [n_ray], closest t [n_ray])."""
+    if pieces is None:
+        pieces = presplit(case["cps"])
+    rays, rp, si, pc = _ws(case, pieces)
+    n = rays.shape[0]
+    counts = np.zeros(n, np.int64)
+    t = np.zeros(n)
+    lib().orc_ray_counts(_p(rays), n, _p(rp), _p(si), _p(pc), _p(pieces["begin"]), _p(pieces["level"]),
+                         int(depth), {"cylinder": 0, "box": 1}[mode], int(nthreads), _p(counts), _p(t))
+    return counts, t
 
 
 def closest_d(rays7, row_ptr, seg_idx, depth, pieces, nthreads=0):

@@ -509,6 +509,170 @@ int64_t orc_presplit_d(const double *cps, int64_t n_seg, int max_level, int thic
     return o.n;
 }
 
+/* ---------------------------------------------- pruning-test statistics */
+
+/*
+ * Fig. 8 compares the number of pruning tests of the oriented bounding
+ * cylinders with axis-aligned boxes in the ray's frame (reading R30; the
+ * boxes in Duff et al.'s frame, below).  Per
+ * ray, each candidate is searched in row order with the closest hit so far
+ * as t_max, with no test before the root's, so that only the bounding volume
+ * differs:
+ *   - cylinders: the traversal of Sec. 3.3 (one test per node visited);
+ *   - boxes: the same subdivision without partition planes.  A node's box is
+ *     [min_k (q_k - r_k), max_k (q_k + r_k)] over its four control points q_k
+ *     and radii r_k (the tube lies in the hull of the control spheres); it is
+ *     hit if it contains the ray's axis (x = y = 0) and meets [0, t_max] in
+ *     z.  At a hit inner node both children's boxes are tested, the one with
+ *     the smaller z_min (the left one on a tie) is searched first, and the
+ *     other is tested again when taken up; without disjoint volumes the
+ *     search does not end at the first leaf hit.  A leaf whose box is hit
+ *     takes the leaf test of Sec. 3.3 (capped cylinder), which finds the
+ *     hits.
+ * Returns the number of bounding-volume tests (boxes) in *count.
+ */
+static int piece_depth(int depth, int level);
+
+/*
+ * A box aligned to the ray's frame depends on the frame's rotation about the
+ * ray (the cylinder test does not).  The boxes use the frame Sec. 3.3 cites,
+ * Duff et al.'s orthonormal basis ("Building an orthonormal basis,
+ * revisited", 2017): with s = sign(w_z), a = -1 / (s + w_z), b = w_x w_y a,
+ * e1 = (1 + s w_x^2 a, s b, -s w_x), e2 = (b, s + w_y^2 a, -w_y).
+ */
+static void duff_frame(const double w[3], double e1[3], double e2[3])
+{
+    double s = copysign(1.0, w[2]);
+    double a = -1.0 / (s + w[2]);
+    double b = w[0] * w[1] * a;
+    e1[0] = 1.0 + s * w[0] * w[0] * a; e1[1] = s * b; e1[2] = -s * w[0];
+    e2[0] = b; e2[1] = s + w[1] * w[1] * a; e2[2] = -w[1];
+}
+
+static void node_points(const node_t *c, v4 q[4])
+{
+    q[0] = c->p;
+    q[1] = add4(c->p, c->t0);
+    q[2] = sub4(add4(c->p, c->d), c->t1);
+    q[3] = add4(c->p, c->d);
+}
+
+static int box_hit(const node_t *c, double tmax)
+{
+    v4 q[4];
+    node_points(c, q);
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = INFINITY; hi[a] = -INFINITY; }
+    for (int k = 0; k < 4; ++k) {
+        double v[3] = {q[k].x, q[k].y, q[k].z};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = dmin(lo[a], v[a] - q[k].w);
+            hi[a] = dmax(hi[a], v[a] + q[k].w);
+        }
+    }
+    return lo[0] <= 0.0 && hi[0] >= 0.0 && lo[1] <= 0.0 && hi[1] >= 0.0 && hi[2] >= 0.0 && lo[2] <= tmax;
+}
+
+static double box_zmin(const node_t *c)
+{
+    v4 q[4];
+    node_points(c, q);
+    double z = INFINITY;
+    for (int k = 0; k < 4; ++k) z = dmin(z, q[k].z - q[k].w);
+    return z;
+}
+
+/* The leaf test of the traversal: capped leaf cylinder, entry max(c0, tmin). */
+static int leaf_test(const node_t *c, double tmax, double *t)
+{
+    double tmin, tm, c0, c1;
+    slab(c, tmax, &tmin, &tm);
+    double r = cons_radius(c);
+    if (!(cylinder(c->p, c->d, r, &c0, &c1) && dmax(c0, tmin) <= dmin(c1, tm))) return 0;
+    *t = dmax(c0, tmin);
+    return *t < tmax;
+}
+
+static void box_visit(const node_t *c, uint32_t size, uint32_t min_size, double *best, int64_t *count)
+{
+    if (size <= min_size) {
+        double t;
+        if (leaf_test(c, *best, &t)) *best = t;
+        return;
+    }
+    v4 dp, tc;
+    split_terms(c, &dp, &tc);
+    node_t L = *c, R = *c;
+    subdivide(&L, 0, dp, tc);
+    subdivide(&R, 1, dp, tc);
+    *count += 2;
+    int hl = box_hit(&L, *best), hr = box_hit(&R, *best);
+    if (hl && hr) {
+        int right_first = box_zmin(&R) < box_zmin(&L);
+        const node_t *a = right_first ? &R : &L, *b = right_first ? &L : &R;
+        box_visit(a, size >> 1, min_size, best, count);
+        *count += 1;
+        if (box_hit(b, *best)) box_visit(b, size >> 1, min_size, best, count);
+    } else if (hl) {
+        box_visit(&L, size >> 1, min_size, best, count);
+    } else if (hr) {
+        box_visit(&R, size >> 1, min_size, best, count);
+    }
+}
+
+/* One curve (ray frame) with t_max: box-pruned search, tests and closest t. */
+static double box_search(const v4 Q[4], int depth, double tmax, int64_t *count)
+{
+    node_t c;
+    node_of_points(Q, &c);
+    double best = tmax;
+    *count += 1;
+    if (box_hit(&c, best)) box_visit(&c, ROOT_SIZE, ROOT_SIZE >> depth, &best, count);
+    return best;
+}
+
+/*
+ * Per ray: pruning tests of its candidates searched in row order with the
+ * closest hit so far as t_max; mode 0 cylinders (node tests of the
+ * traversal), mode 1 boxes.  counts: n_ray int64; t_out (nullable): the
+ * closest hit found (inf on a miss).
+ */
+void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+                    const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+                    int depth, int mode, int nthreads, int64_t *counts, double *t_out)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n_ray; ++i) {
+        ray_t r = make_ray_f(rays + 8 * i);
+        if (mode == 1) duff_frame(r.w, r.e1, r.e2);
+        double best = r.tmax;
+        int64_t n = 0;
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+            int32_t s = seg_idx[j];
+            for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
+                v4 Q[4];
+                to_ray_frame(&r, piece_cp + 16 * k, Q);
+                int d = piece_depth(depth, piece_level[k]);
+                if (mode == 0) {
+                    orc_hit h;
+                    traverse(Q, d, best, &h);
+                    n += h.nodes;
+                    if (h.hit && h.t < best) best = h.t;
+                } else {
+                    best = box_search(Q, d, best, &n);
+                }
+            }
+        }
+        counts[i] = n;
+        if (t_out) t_out[i] = best < r.tmax ? best : INFINITY;
+    }
+}
+
 /* ------------------------------------------------------ quadratic curves */
 
 /*

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libfiberx.so")
-SOURCES = ["filter_kernels.cu", "lane_kernels.cu", "scan_kernels.cu", "ray_kernels.cu", "normal_kernels.cu", "trace_kernels.cu", "warp_kernels.cu", "backward.cu", "fiberx_api.cu",
+SOURCES = ["filter_kernels.cu", "lane_kernels.cu", "scan_kernels.cu", "ray_kernels.cu", "normal_kernels.cu", "count_kernels.cu", "trace_kernels.cu", "warp_kernels.cu", "backward.cu", "fiberx_api.cu",
            "noalloc.cu", "peak.cu", "presplit.cpp"]
 HEADERS = ["trace.cuh", "internal.h", "presplit.h", os.path.join(ROOT, "include", "fiberx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -411,6 +411,18 @@ fx_status intersect_backward(const fx_fibers* f, const float* rays, int64_t n_ra
   return FX_OK;
 }
 
+fx_status intersect_counts(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
+                           const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags,
+                           uint32_t* counts, void* stream) {
+  fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  if (st != FX_OK) return st;
+  if (n_ray > 0 && !counts) return fail(FX_EINVAL, "null counts output");
+  if (!f->identity) return fail(FX_EUNSUPPORTED, "counts need segments that are single level-0 pieces");
+  fx::TraceArgs a = make_args(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  FX_CUDA(fx::launch_counts(a, counts, (flags & FX_COUNT_BOXES) != 0, flags, (cudaStream_t)stream));
+  return FX_OK;
+}
+
 fx_status intersect_normals(const fx_fibers* f, const float* rays, int64_t n_ray, const float* tu,
                             const int32_t* seg, const int32_t* leaf, int32_t depth, uint32_t flags,
                             float* normal, void* stream) {

@@ -111,6 +111,9 @@ cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int 
 cudaError_t launch_normals(const TraceArgs &a, const float4 *seg_cp, float *normal, uint32_t flags,
                            cudaStream_t s);
 
+// count_kernels.cu: per-ray pruning-test counts, cylinders or boxes (Fig. 8)
+cudaError_t launch_counts(const TraceArgs &a, uint32_t *counts, bool box, uint32_t flags, cudaStream_t s);
+
 // peak.cu: FP32 FMA microbenchmark (synchronises s); flops = FMA flops of the
 // timed launch
 cudaError_t fma_peak(int sm_count, int blocks_per_sm, int iters, float *ms, double *flops, cudaStream_t s);

@@ -29,6 +29,7 @@ FX_FAST_MATH = 0x2
 FX_POLISH_FP64 = 0x4
 FX_COUNT = 0x8
 FX_CHECK_INDEX = 0x10
+FX_COUNT_BOXES = 0x20
 
 FX_VARIANT_AUTO = 0
 FX_VARIANT_LANE = 1
@@ -39,7 +40,7 @@ FX_VARIANT_RAY = 5
 
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_upload_quadratic", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
-           "intersect_backward", "intersect_normals", "intersect_closest_host", "intersect_closest_noalloc",
+           "intersect_backward", "intersect_normals", "intersect_counts", "intersect_closest_host", "intersect_closest_noalloc",
            "fx_set_launch",
            "fx_get_launch", "fx_counters", "fx_stream_status", "fx_fma_peak", "fx_last_error", "fx_version"]
 NOALLOC_MAX_RAYS = 1 << 20
@@ -100,6 +101,8 @@ def lib():
             L.intersect_pairs.restype = i32
             L.intersect_backward.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
             L.intersect_backward.restype = i32
+            L.intersect_counts.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp]
+            L.intersect_counts.restype = i32
             L.intersect_normals.argtypes = [vp, vp, i64, vp, vp, vp, i32, u32, vp, vp]
             L.intersect_normals.restype = i32
             L.intersect_closest_host.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
@@ -287,6 +290,18 @@ def intersect_pairs(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, s
     _check(lib().intersect_pairs(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx), n_pair,
                                  int(depth), int(flags), _ptr(tu), _ptr(lf), _stream(stream)))
     return tu, lf
+
+
+def intersect_counts(fibers, rays, row_ptr, seg_idx, depth, boxes=False, flags=0, stream=None):
+    """Per-ray pruning-test counts [n_ray] uint32 as int64 (Fig. 8): oriented
+    cylinders, or ray-frame axis-aligned boxes with boxes=True."""
+    import torch
+    rays, row_ptr, seg_idx = _inputs(fibers, rays, row_ptr, seg_idx)
+    n = torch.zeros(rays.shape[0], dtype=torch.int32, device=fibers.device)
+    _check(lib().intersect_counts(fibers.handle, _ptr(rays), rays.shape[0], _ptr(row_ptr), _ptr(seg_idx),
+                                  seg_idx.numel(), int(depth), int(flags) | (FX_COUNT_BOXES if boxes else 0),
+                                  _ptr(n), _stream(stream)))
+    return n.to(torch.int64) & 0xffffffff
 
 
 def intersect_normals(fibers, rays, tu, seg, leaf, depth, flags=0, stream=None, out=None):

@@ -343,6 +343,27 @@ def single_fiber_case(klass: str, n_ray: int, seed: int = SEED_BASE + 5):
     return dict(cps=cps, rays=rays, row_ptr=row_ptr, seg_idx=seg_idx, name="single_%s" % klass)
 
 
+def single_fiber_image_case(klass: str, res: int = 512, seed: int = SEED_BASE + 7):
+    """One segment of the curvature class seen by a res x res pinhole camera
+    (the setting of Fig. 8's per-pixel heat maps): radii 0.005-0.05 of the
+    segment's length; the camera looks at the chord's midpoint from 2.5
+    segment lengths away, perpendicular to the chord, with a 30 degree field
+    of view; every ray lists the segment.
+    Returns the case with `pixel` (row-major pixel of each ray) and `res`."""
+    g = rng(seed + 7919 * list(SWEEP_JITTER).index(klass))
+    cps = sweep_segments(g, 1, SWEEP_JITTER[klass])
+    cps[..., 3] *= 5.0  # radii 0.005-0.05 of the length: a fiber some pixels wide
+    c = cps[0].astype(np.float64)
+    mid = 0.5 * (c[0, :3] + c[3, :3])
+    chord = _normalize((c[3, :3] - c[0, :3])[None])[0]
+    side = _perp_unit(g, chord[None])[0]
+    eye = mid + 2.5 * side
+    rays, pix = pinhole_rays(res, res, eye=eye, look_at=mid, up=tuple(np.cross(side, chord)), vfov_deg=30.0)
+    n = rays.shape[0]
+    return dict(cps=cps, rays=rays, row_ptr=np.arange(n + 1, dtype=np.int32), seg_idx=np.zeros(n, np.int32),
+                pixel=pix, res=res, name="image_%s" % klass)
+
+
 def quadratic_segments(g, n, jitter, L=1.0):
     """Quadratic segments [n, 3, 4]: p0 ~ U[-10, 10]^3, p2 = p0 + L u (u
     uniform on the sphere), p1 = the chord's midpoint + jitter * L * (a point

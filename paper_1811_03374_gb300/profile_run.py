@@ -14,11 +14,18 @@ mean launch time measured with CUDA events after one untimed launch.
     --backward 1       also times the adjoint (intersect_backward) of the
                        loss sum_i w_i t_i, w ~ N(0, 1), after each forward,
                        and reports the backward / forward time ratio
+    --counts 1         per-ray pruning-test counts (intersect_counts, Fig. 8)
+                       with oriented cylinders and with ray-frame boxes: mean,
+                       99th percentile and maximum per depth; for image-<class>
+                       (one fiber seen by a 512 x 512 camera) --pgm DIR also
+                       writes the per-pixel counts as log-scaled PGM images
 """
 import argparse
 import json
 import os
 import sys
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -37,7 +44,21 @@ def load(name):
         return I.aimed_hair_case(1_000_000)
     if name.startswith("single-"):
         return I.single_fiber_case(name.split("-", 1)[1], 1 << 20)
+    if name.startswith("image-"):
+        return I.single_fiber_image_case(name.split("-", 1)[1], 512)
     raise SystemExit("unknown workload %s" % name)
+
+
+def write_pgm(path, counts, case):
+    """Per-pixel counts as an 8-bit PGM: log2(1 + count), 255 at 2^16."""
+    res = case["res"]
+    img = np.zeros(res * res)
+    img[case["pixel"]] = np.log2(1.0 + counts.astype(np.float64))
+    img = np.clip(img * (255.0 / 16.0), 0, 255).astype(np.uint8).reshape(res, res)
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    with open(path, "wb") as f:
+        f.write(b"P5\n%d %d\n255\n" % (res, res))
+        f.write(img.tobytes())
 
 
 def depth_list(spec):
@@ -59,6 +80,8 @@ def main():
     p.add_argument("--chunk", type=int, default=32)
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--backward", type=int, default=0)
+    p.add_argument("--counts", type=int, default=0)
+    p.add_argument("--pgm", default=None)
     a = p.parse_args()
 
     import torch
@@ -75,6 +98,23 @@ def main():
     n_pair = len(case["seg_idx"])
     w = torch.from_numpy(I.hit_weights(rays.shape[0])).to(dev)
     grad = torch.zeros((fib.n_seg, 4, 4), dtype=torch.float32, device=dev)
+    if a.counts:
+        for depth in (depth_list(a.depths) if a.depths else [a.depth]):
+            rec = {"workload": a.workload, "depth": depth, "rays": int(rays.shape[0])}
+            for mode in ("cylinder", "box"):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                n = F.intersect_counts(fib, rays, rp, si, depth, boxes=mode == "box", flags=flags)
+                e.record()
+                torch.cuda.synchronize()
+                n = n.cpu().numpy()
+                rec[mode] = {"mean": float(n.mean()), "p99": float(np.percentile(n, 99)), "max": int(n.max()),
+                             "total": int(n.sum()), "ms": s.elapsed_time(e)}
+                if a.pgm and "pixel" in case:
+                    write_pgm(os.path.join(a.pgm, "%s_d%02d_%s.pgm" % (a.workload, depth, mode)), n, case)
+            print(json.dumps(rec), flush=True)
+        fib.close()
+        return
     for depth in (depth_list(a.depths) if a.depths else [a.depth]):
         out = F.intersect_closest(fib, rays, rp, si, depth, flags)
         torch.cuda.synchronize()

@@ -1,0 +1,76 @@
+"""Pins of the oracle's pruning-test statistic (Fig. 8; reading R30): the
+cylinder counts are the traversal's node tests, the box search finds the same
+hits, hand-counted box cases, and the figure's claim that box tests grow
+exponentially with the depth while cylinder tests grow by about one per level
+(CPU only)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_03374_gb300 import inputs as I
+from tests import _geom as G
+
+
+def _one(ray7, cp):
+    """A case of one ray and one curve."""
+    r = ray7
+    rays = I.pack_rays(r[None, :3], r[None, 3:6] / np.linalg.norm(r[3:6]))
+    return dict(cps=np.asarray(cp, np.float32)[None], rays=rays, row_ptr=np.array([0, 1], np.int32),
+                seg_idx=np.array([0], np.int32))
+
+
+@pytest.mark.parametrize("depth", [0, 3, 8, 15])
+def test_cylinder_counts_are_traversal_node_tests(depth):
+    case = I.sweep_case("moderate", 300, forced_hits=True)
+    counts, t = O.ray_counts(case, depth, "cylinder")
+    pieces = O.presplit(case["cps"])
+    for i in range(300):
+        if np.diff(pieces["begin"])[i] != 1:
+            continue  # pre-split: several pieces, each with its own count
+        h = O.intersect(O.ray7_from_packed(case["rays"][i]), pieces["cp"][pieces["begin"][i]], depth)
+        assert counts[i] == h.nodes
+        assert (h.hit and abs(t[i] - h.t) <= 1e-12 * h.t) or (not h.hit and np.isinf(t[i]))
+
+
+@pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
+def test_box_search_finds_the_same_hits(klass):
+    # both searches end in the same leaf test; they agree wherever every leaf
+    # cylinder the ray meets lies inside the bounding volumes of its
+    # ancestors in both hierarchies.  A leaf's conservative cylinder can reach
+    # out of a box (and of its parent's cylinder): at depth 2 a few rays in a
+    # hundred differ, deeper at most one in a thousand
+    case = I.single_fiber_case(klass, 3000)
+    for depth, frac in ((2, 0.95), (4, 0.995), (7, 0.999), (12, 0.999)):
+        _, tc = O.ray_counts(case, depth, "cylinder")
+        _, tb = O.ray_counts(case, depth, "box")
+        same = np.isclose(tb, tc, rtol=1e-12, atol=0) | (np.isinf(tb) & np.isinf(tc))
+        assert same.mean() >= frac, (depth, same.mean())
+
+
+def test_box_counts_by_hand():
+    # a straight fiber along x from -1 to 1, radius 0.1; rays straight down
+    cp = np.array([[-1.0, 0, 0, 0.1], [-1 / 3, 0, 0, 0.1], [1 / 3, 0, 0, 0.1], [1.0, 0, 0, 0.1]])
+    down = np.array([0.0, 0, -1.0])
+    at = lambda x: _one(G.ray7(np.array([x, 0.0, 3.0]), down), cp)
+    # depth 0: the root is the leaf -- one box test
+    assert O.ray_counts(at(0.5), 0, "box")[0][0] == 1
+    # depth 1, ray at x = 0.5: root box, both children tested, only the right
+    # one holds x = 0.5 (the left box ends at 0.1)
+    assert O.ray_counts(at(0.5), 1, "box")[0][0] == 3
+    # ray at x = 0: both children hit; the second is tested again when taken up
+    assert O.ray_counts(at(0.0), 1, "box")[0][0] == 4
+    # a ray passing beside the root box: one test
+    assert O.ray_counts(at(1.5), 5, "box")[0][0] == 1
+
+
+def test_fig8_boxes_grow_exponentially_cylinders_linearly():
+    case = I.single_fiber_case("moderate", 2000)
+    cyl, box = [], []
+    depths = [10, 13, 16, 19]
+    for d in depths:
+        cyl.append(O.ray_counts(case, d, "cylinder")[0].mean())
+        box.append(O.ray_counts(case, d, "box")[0].mean())
+    for k in range(1, len(depths)):
+        assert box[k] >= 2.0 * box[k - 1], box          # at least x2 per 3 levels
+        assert cyl[k] - cyl[k - 1] <= 3.0 * 1.5, cyl     # about one per level
+    assert box[-1] > 20 * cyl[-1]

@@ -13,7 +13,8 @@ import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_primitives.py", "tests/test_oracle_traversal.py",
-        "tests/test_oracle_grad.py", "tests/test_oracle_normals.py", "tests/test_oracle_quadratic.py"]
+        "tests/test_oracle_grad.py", "tests/test_oracle_normals.py", "tests/test_oracle_quadratic.py",
+        "tests/test_oracle_counts.py"]
 
 MUTATIONS = {
     "split_dp_coefficient": ("*dp = add4(add4(mul4(0.375, c->t0)", "*dp = add4(add4(mul4(0.125, c->t0)"),
@@ -46,6 +47,8 @@ MUTATIONS = {
                              "n[i] = xx * r.e2[i] + yy * r.e1[i] + zz * r.w[i];"),
     "normal_axis_point_unprojected": ("v4 ap = add4(c.p, mul4(ul, c.d));", "v4 ap = c.p;"),
     "normal_cap_points": ("int a = cap0 ? 0 : 3, b = cap0 ? 1 : 2;", "int a = cap0 ? 0 : 3, b = cap0 ? 1 : 1;"),
+    "box_dilation_dropped": ("lo[a] = dmin(lo[a], v[a] - q[k].w);", "lo[a] = dmin(lo[a], v[a]);"),
+    "box_retest_uncounted": ("        *count += 1;\n        if (box_hit(b, *best))", "        if (box_hit(b, *best))"),
     "quadratic_elevation_weight": ("cp16[4 + a] = (p0 + 2.0 * p1) / 3.0;", "cp16[4 + a] = (2.0 * p0 + p1) / 3.0;"),
     "quadratic_constraint_sign": ("return dot3(a, b) <= 0.0;", "return dot3(a, b) >= 0.0;"),
     "normal_cap_plane_sign": ("cap0 = dot3(sub4(x, Q[0]), a0) / sqrt(dot3(a0, a0)) >= -tol;",
