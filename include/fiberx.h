@@ -68,7 +68,7 @@ typedef struct fx_fibers fx_fibers; /* opaque; owns the device copy of the fiber
 
 typedef struct {
     int32_t max_presplit; /* levels of dyadic pre-split for invalid curves, 0..8 (default 8) */
-    int32_t thick_check;  /* 1 (default): sampled end-plane check for thick fibers (Sec. 3.4) */
+    int32_t thick_check;  /* 1 (default): exact end-plane check for thick fibers (Sec. 3.4) */
 } fx_upload_opts;
 
 typedef struct {
@@ -118,9 +118,11 @@ typedef struct {
  * the caller keeps ownership.  opts may be NULL (defaults).
  *
  * Each segment is checked in FP64 against the five inequalities of Sec. 3.4
- * (App. B.2) and a sampled end-plane check for thick fibers (Sec. 3.4,
- * Fig. 7); failing curves are halved at u = 1/2 recursively ("subdivided
- * beforehand", Sec. 3.4) up to max_presplit levels.  A piece at level k is
+ * (App. B.2) and an exact end-plane check for thick fibers (Sec. 3.4,
+ * Fig. 7: no end plane cuts the tube swept by the largest control radius,
+ * decided on polynomials in u by Bernstein subdivision); failing curves are
+ * halved at u = 1/2 recursively (Sec. 3.4 requires such curves to be split
+ * first) up to max_presplit levels.  A piece at level k is
  * later traversed to depth d - k, so its leaves coincide with the unsplit
  * curve's.  Pieces still failing at the last level are kept and counted as
  * unsupported (not an error).

@@ -387,17 +387,103 @@ int orc_valid_cubic(const double *cp)
 
 static double norm3(v4 a) { return sqrt(dot3(a, a)); }
 
+/* ------------------------------------------- polynomials on [0, 1] */
+
+#define PMAX 11 /* degree <= 10 */
+typedef struct { double a[PMAX]; int n; } poly_t; /* power basis, a[k] u^k */
+
+static poly_t pz(int n) { poly_t p; memset(&p, 0, sizeof p); p.n = n; return p; }
+
+static poly_t padd(poly_t x, poly_t y, double sy)
+{
+    poly_t r = pz(x.n > y.n ? x.n : y.n);
+    for (int k = 0; k <= x.n; ++k) r.a[k] += x.a[k];
+    for (int k = 0; k <= y.n; ++k) r.a[k] += sy * y.a[k];
+    return r;
+}
+
+static poly_t pmul(poly_t x, poly_t y)
+{
+    poly_t r = pz(x.n + y.n);
+    for (int i = 0; i <= x.n; ++i)
+        for (int j = 0; j <= y.n; ++j) r.a[i + j] += x.a[i] * y.a[j];
+    return r;
+}
+
+/* x / (u - root), x having that root (the remainder is dropped) */
+static poly_t pdiv_root(poly_t x, double root)
+{
+    poly_t q = pz(x.n - 1);
+    double c = x.a[x.n];
+    for (int k = x.n - 1; k >= 0; --k) {
+        q.a[k] = c;
+        c = x.a[k] + root * c;
+    }
+    return q;
+}
+
 /*
- * Sampled end-plane check for thick fibers (Sec. 3.4, Fig. 7; reading R13).
- * The fiber surface point at parameter u nearest the end plane lies in the
- * normal plane at u, displaced by the largest radius rbar along the
- * Gram-Schmidt projection n_u of the plane normal.  The end plane through p3
- * (normal c'(1)) crops the surface if <p3 - c(u), t1^> < rbar |t1^ - <t1^, tu^> tu^|
- * for some u; likewise for the start plane through p0.  Checked at u = i/32
- * and, at the end points themselves, as rbar * curvature < 1.  A zero end
- * tangent fails.
+ * x >= 0 on [0, 1].  In the Bernstein basis of degree n on an interval,
+ * b_k = sum_{i <= k} C(k, i) / C(n, i) a_i on [0, 1]; the polynomial lies
+ * between the smallest and largest b_k, and b_0, b_n are its end values.  So
+ * all b_k >= 0 proves x >= 0, a negative end value disproves it, and
+ * otherwise the interval is halved (de Casteljau) and both halves checked.
+ * Values within 1e-12 of the largest coefficient count as zero (FP64
+ * rounding of the coefficients); 40 halvings without a decision count as a
+ * violation.
  */
-#define THICK_SAMPLES 32
+static int bern_nonneg(const double *b, int n, double tol, int depth)
+{
+    if (b[0] < -tol || b[n] < -tol) return 0;
+    int all = 1;
+    for (int k = 0; k <= n; ++k) all &= b[k] >= -tol;
+    if (all) return 1;
+    if (depth >= 40) return 0;
+    double w[PMAX], L[PMAX], R[PMAX];
+    for (int k = 0; k <= n; ++k) w[k] = b[k];
+    for (int lvl = 0; lvl <= n; ++lvl) {
+        L[lvl] = w[0];
+        R[n - lvl] = w[n - lvl];
+        for (int k = 0; k < n - lvl; ++k) w[k] = 0.5 * (w[k] + w[k + 1]);
+    }
+    return bern_nonneg(L, n, tol, depth + 1) && bern_nonneg(R, n, tol, depth + 1);
+}
+
+static double binom(int n, int k)
+{
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+static int nonneg01(poly_t x)
+{
+    double b[PMAX], m = 0.0;
+    for (int k = 0; k <= x.n; ++k) {
+        b[k] = 0.0;
+        for (int i = 0; i <= k; ++i) b[k] += binom(k, i) / binom(x.n, i) * x.a[i];
+        m = dmax(m, fabs(b[k]));
+    }
+    return bern_nonneg(b, x.n, 1e-12 * m, 0);
+}
+
+/*
+ * The end-plane condition for thick fibers (Sec. 3.4, Fig. 7): the surface
+ * point of the cross-section at u that comes closest to the end plane
+ * through p3 with normal n1 = p3 - p2 lies r sin(theta(u)) beyond c(u)
+ * towards it, theta(u) the angle between c'(u) and n1 (the Gram-Schmidt
+ * displacement of the paper); with rbar the largest control radius the
+ * fiber is not cropped when <p3 - c(u), n1> / |n1| >= rbar sin(theta(u))
+ * for all u in [0, 1].  With t = c' / 3 and D1 = <p3 - c, n1> this is
+ * D1 >= 0 and D1^2 |t|^2 - rbar^2 |n1 x t|^2 >= 0 (both sides multiplied by
+ * |n1| |t|), polynomials of degree 3 and 10 in u with a simple and a double
+ * root at u = 1, where the fiber meets its own end plane; divided by them,
+ * both must be non-negative on [0, 1] (at u = 1 the second reduces to
+ * rbar * curvature <= 1).  The start plane through p0 with normal p1 - p0
+ * likewise, roots at u = 0.  The paper speaks of a quartic; these are the
+ * same conditions checked exactly on the polynomials (reading R13).
+ * Returns 1 if neither end plane crops the fiber.
+ */
 int orc_thick_ok(const double *cp)
 {
     v4 P[4];
@@ -406,33 +492,50 @@ int orc_thick_ok(const double *cp)
         P[k] = load_cp(cp, k);
         rbar = dmax(rbar, P[k].w);
     }
-    v4 ta = bez_deriv3(P, 0.0), tb = bez_deriv3(P, 1.0);
-    double la = norm3(ta), lb = norm3(tb);
-    if (!(la > 0.0) || !(lb > 0.0)) return 0;
-    v4 na = mul4(1.0 / la, ta), nb = mul4(1.0 / lb, tb);
-    for (int i = 0; i <= THICK_SAMPLES; ++i) {
-        double u = (double)i / THICK_SAMPLES;
-        v4 tu = bez_deriv3(P, u);
-        double lu = norm3(tu);
-        if (!(lu > 0.0)) return 0;
-        v4 nu = mul4(1.0 / lu, tu);
-        v4 cu = bez_eval(P, u);
-        if (i < THICK_SAMPLES) { /* end plane */
-            v4 g = sub4(nb, mul4(dot3(nb, nu), nu));
-            if (dot3(sub4(P[3], cu), nb) < rbar * norm3(g)) return 0;
-        }
-        if (i > 0) { /* start plane */
-            v4 g = sub4(na, mul4(dot3(na, nu), nu));
-            if (dot3(sub4(cu, P[0]), na) < rbar * norm3(g)) return 0;
-        }
+    double pc[3][4];
+    for (int j = 0; j < 3; ++j) {
+        double p0 = (&P[0].x)[j], p1 = (&P[1].x)[j], p2 = (&P[2].x)[j], p3 = (&P[3].x)[j];
+        pc[j][0] = p0;
+        pc[j][1] = 3.0 * (p1 - p0);
+        pc[j][2] = 3.0 * (p0 - 2.0 * p1 + p2);
+        pc[j][3] = p3 - 3.0 * p2 + 3.0 * p1 - p0;
     }
+    poly_t c[3], t[3];
+    for (int j = 0; j < 3; ++j) {
+        c[j] = pz(3);
+        for (int k = 0; k < 4; ++k) c[j].a[k] = pc[j][k];
+        t[j] = pz(2);
+        for (int k = 0; k < 3; ++k) t[j].a[k] = (k + 1) * pc[j][k + 1] / 3.0;
+    }
+    poly_t T = pz(0);
+    for (int j = 0; j < 3; ++j) T = padd(T, pmul(t[j], t[j]), 1.0);
+    v4 nrm[2] = {sub4(P[1], P[0]), sub4(P[3], P[2])};
     for (int e = 0; e < 2; ++e) {
-        double u = (double)e;
-        v4 d1 = mul4(3.0, bez_deriv3(P, u)), d2 = bez_deriv2(P, u);
-        v4 cr = V(d1.y * d2.z - d1.z * d2.y, d1.z * d2.x - d1.x * d2.z, d1.x * d2.y - d1.y * d2.x, 0.0);
-        double l1 = norm3(d1);
-        double kappa = norm3(cr) / (l1 * l1 * l1);
-        if (rbar * kappa >= 1.0) return 0;
+        v4 n = nrm[e];
+        double nn = dot3(n, n);
+        if (!(nn > 0.0)) return 0;
+        poly_t D = pz(0), G = pz(0);
+        for (int j = 0; j < 3; ++j) {
+            double nj = (&n.x)[j];
+            poly_t cj = c[j];
+            if (e == 1) { /* <p3 - c, n1> */
+                for (int k = 0; k <= 3; ++k) cj.a[k] = -cj.a[k];
+                cj.a[0] += (&P[3].x)[j];
+            } else {      /* <c - p0, n0> */
+                cj.a[0] -= (&P[0].x)[j];
+            }
+            poly_t sj = pz(0); sj.a[0] = nj;
+            D = padd(D, pmul(sj, cj), 1.0);
+            G = padd(G, pmul(sj, t[j]), 1.0);
+        }
+        poly_t X = padd(T, pmul(G, G), -1.0 / nn);
+        for (int k = 0; k <= X.n; ++k) X.a[k] *= nn; /* |n|^2 T - <n, t>^2 = |n x t|^2 */
+        poly_t Pq = padd(pmul(pmul(D, D), T), X, -rbar * rbar);
+        double root = e == 1 ? 1.0 : 0.0;
+        poly_t E = pdiv_root(D, root);
+        if (e == 1) for (int k = 0; k <= E.n; ++k) E.a[k] = -E.a[k]; /* D1 = (1 - u) E */
+        poly_t Q = pdiv_root(pdiv_root(Pq, root), root);
+        if (!nonneg01(E) || !nonneg01(Q)) return 0;
     }
     return 1;
 }
@@ -451,8 +554,8 @@ void orc_split_half(const double *cp, double *L, double *R)
 }
 
 /*
- * Pre-split (Sec. 3.4: curves violating the constraints "must be subdivided
- * beforehand"; reading R15): a curve failing the constraints or the sampled
+ * Pre-split (Sec. 3.4: a curve violating the constraints has to be split before it
+ * is traversed; reading R15): a curve failing the constraints or the
  * thick-fiber check is halved at u = 1/2, recursively, left before right, up
  * to max_level levels.  A piece still failing at max_level is kept and
  * flagged unsupported (flag bit 0).
@@ -678,7 +781,7 @@ void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, co
 /*
  * App. B.1: a quadratic curve (p0, p1, p2) can be split recursively at the
  * domain centre into subcurves with disjoint bounding volumes when
- * <p1 - p0, p1 - p2> <= 0 (positions).  (The lemma states "if and only if",
+ * <p1 - p0, p1 - p2> <= 0 (positions).  (The lemma claims an equivalence,
  * but its two one-sided conditions <p1 - p0, p2 - p0> >= 0 and
  * <p1 - p2, p0 - p2> >= 0 do not imply the combined one; the combined one is
  * the one its second lemma carries to every subcurve.  Reading R29.)

@@ -3,9 +3,10 @@
 //
 // Sec. 3.4: disjoint bounding volumes under recursive bisection need five
 // inequalities on the control points (App. B.2 proves they suffice and are
-// inherited by both halves); curves violating them "must be subdivided
-// beforehand".  Thick fibers can still cross a partitioning plane; Sec. 3.4
-// reduces the test to the two end planes of a fiber (Fig. 7).  Here a curve
+// inherited by both halves); a curve violating them has to be split before
+// it is traversed.  Thick fibers can still cross a partitioning plane;
+// Sec. 3.4 reduces the test to the two end planes of a fiber (Fig. 7),
+// checked here exactly on polynomials in the Bernstein basis.  Here a curve
 // failing either test is halved at u = 1/2 recursively, left half first, up
 // to a maximum level; pieces still failing at that level are kept and marked
 // unsupported.  Each piece is stored as its (p, d, t0, t1) tuple (Sec. 3.1),
@@ -44,76 +45,131 @@ bool constraints_hold(const Curve& c) {
          dot(a, e) >= 0.0;
 }
 
-P4 point_at(const Curve& c, double u) {
-  const double s = 1.0 - u;
-  const double w0 = s * s * s, w1 = 3.0 * u * s * s, w2 = 3.0 * u * u * s, w3 = u * u * u;
-  P4 r;
-  for (int k = 0; k < 4; ++k) r.v[k] = w0 * c[0].v[k] + w1 * c[1].v[k] + w2 * c[2].v[k] + w3 * c[3].v[k];
+// Polynomials on [0, 1] in the Bernstein basis of their degree (at most 10).
+struct Bern {
+  int n = 0;
+  double b[11] = {0};
+};
+
+double choose(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
   return r;
 }
 
-// Tangent direction (c'(u) up to the factor 3).
-P4 tangent_at(const Curve& c, double u) {
-  const double s = 1.0 - u;
-  P4 r;
-  for (int k = 0; k < 4; ++k)
-    r.v[k] = s * s * (c[1].v[k] - c[0].v[k]) + 2.0 * u * s * (c[2].v[k] - c[1].v[k]) +
-             u * u * (c[3].v[k] - c[2].v[k]);
+// (f g)_k = sum_{i + j = k} C(m, i) C(n, j) / C(m + n, k) f_i g_j
+Bern product(const Bern& f, const Bern& g) {
+  Bern r;
+  r.n = f.n + g.n;
+  for (int i = 0; i <= f.n; ++i)
+    for (int j = 0; j <= g.n; ++j)
+      r.b[i + j] += choose(f.n, i) * choose(g.n, j) / choose(r.n, i + j) * f.b[i] * g.b[j];
   return r;
 }
 
-// Curvature |c' x c''| / |c'|^3 at u.
-double curvature_at(const Curve& c, double u) {
-  const P4 t = tangent_at(c, u);
-  double d1[3], d2[3];
-  for (int k = 0; k < 3; ++k) {
-    d1[k] = 3.0 * t.v[k];
-    const double a = c[2].v[k] - 2.0 * c[1].v[k] + c[0].v[k];
-    const double b = c[3].v[k] - 2.0 * c[2].v[k] + c[1].v[k];
-    d2[k] = 6.0 * ((1.0 - u) * a + u * b);
+// degree elevation to n
+Bern raise(Bern f, int n) {
+  while (f.n < n) {
+    Bern r;
+    r.n = f.n + 1;
+    for (int k = 0; k <= r.n; ++k) {
+      const double a = k > 0 ? f.b[k - 1] * k / r.n : 0.0;
+      const double c = k < r.n ? f.b[k] * (r.n - k) / r.n : 0.0;
+      r.b[k] = a + c;
+    }
+    f = r;
   }
-  const double cx = d1[1] * d2[2] - d1[2] * d2[1], cy = d1[2] * d2[0] - d1[0] * d2[2],
-               cz = d1[0] * d2[1] - d1[1] * d2[0];
-  const double l = std::sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
-  return std::sqrt(cx * cx + cy * cy + cz * cz) / (l * l * l);
+  return f;
 }
 
-// Sampled end-plane check (Sec. 3.4, Fig. 7): the surface point of the
-// cross-section at u closest to an end plane sits rbar * |sin(angle between
-// c'(u) and the plane normal)| beyond c(u) towards it; the plane crops the
-// fiber if that exceeds the distance of c(u) from the plane.  Samples
-// u = i / 32, plus rbar * curvature < 1 at both ends.
-constexpr int kThickSamples = 32;
+Bern combine(const Bern& f, double sf, const Bern& g, double sg) {
+  const int n = std::max(f.n, g.n);
+  const Bern a = raise(f, n), c = raise(g, n);
+  Bern r;
+  r.n = n;
+  for (int k = 0; k <= n; ++k) r.b[k] = sf * a.b[k] + sg * c.b[k];
+  return r;
+}
 
+// f = (1 - u) h for f vanishing at u = 1: (1 - u) B^{n-1}_i = (n - i) / n B^n_i
+Bern div_one_minus_u(const Bern& f) {
+  Bern h;
+  h.n = f.n - 1;
+  for (int i = 0; i <= h.n; ++i) h.b[i] = f.b[i] * f.n / (f.n - i);
+  return h;
+}
+
+// f = u h for f vanishing at u = 0: u B^{n-1}_i = (i + 1) / n B^n_{i+1}
+Bern div_u(const Bern& f) {
+  Bern h;
+  h.n = f.n - 1;
+  for (int i = 0; i <= h.n; ++i) h.b[i] = f.b[i + 1] * f.n / (i + 1);
+  return h;
+}
+
+// f >= 0 on [0, 1]: all coefficients >= 0 proves it (convex hull), a
+// negative end value (b_0 or b_n) disproves it, otherwise both halves
+// (de Casteljau at 1/2) are checked.  Coefficients within tol of zero count
+// as zero; an undecided 40th halving counts as a violation.
+bool nonneg(const double* b, int n, double tol, int depth) {
+  if (b[0] < -tol || b[n] < -tol) return false;
+  bool all = true;
+  for (int k = 0; k <= n; ++k) all = all && b[k] >= -tol;
+  if (all) return true;
+  if (depth >= 40) return false;
+  double w[11], L[11], R[11];
+  std::memcpy(w, b, sizeof(double) * (n + 1));
+  for (int lvl = 0; lvl <= n; ++lvl) {
+    L[lvl] = w[0];
+    R[n - lvl] = w[n - lvl];
+    for (int k = 0; k + lvl < n; ++k) w[k] = 0.5 * (w[k] + w[k + 1]);
+  }
+  return nonneg(L, n, tol, depth + 1) && nonneg(R, n, tol, depth + 1);
+}
+
+bool nonneg01(const Bern& f) {
+  double m = 0.0;
+  for (int k = 0; k <= f.n; ++k) m = std::max(m, std::fabs(f.b[k]));
+  return nonneg(f.b, f.n, 1e-12 * m, 0);
+}
+
+// End-plane check for thick fibers (Sec. 3.4, Fig. 7).  The cross-section at
+// u reaches rbar sin(theta(u)) beyond c(u) towards an end plane, theta the
+// angle between c'(u) and the plane's normal n (Gram-Schmidt displacement);
+// rbar is the largest control radius.  The fiber is not cropped by the end
+// plane through p3, n = p3 - p2, if D = <p3 - c(u), n> >= 0 and
+// D^2 |t|^2 >= rbar^2 |n x t|^2 (t = c' / 3) for all u in [0, 1]: degree 3
+// and 10 with a simple and a double root at u = 1, where the fiber meets its
+// own end plane, which are divided out before both are checked
+// non-negative; at u = 1 the second becomes rbar * curvature <= 1.  The
+// start plane through p0, n = p1 - p0, likewise with the roots at u = 0.
 bool thick_ok(const Curve& c) {
   double rbar = 0.0;
   for (const P4& p : c) rbar = std::max(rbar, p.v[3]);
-  const P4 ts = tangent_at(c, 0.0), te = tangent_at(c, 1.0);
-  const double ls = len(ts), le = len(te);
-  if (!(ls > 0.0) || !(le > 0.0)) return false;
-  for (int i = 0; i <= kThickSamples; ++i) {
-    const double u = double(i) / kThickSamples;
-    const P4 tu = tangent_at(c, u);
-    const double lu = len(tu);
-    if (!(lu > 0.0)) return false;
-    const P4 cu = point_at(c, u);
-    if (i < kThickSamples) {
-      // end plane through p3 with normal te / le
-      const double ct = dot(te, tu) / (le * lu);
-      P4 g = axpy(-ct, P4{{tu.v[0] / lu, tu.v[1] / lu, tu.v[2] / lu, 0}},
-                  P4{{te.v[0] / le, te.v[1] / le, te.v[2] / le, 0}});
-      const double dist = dot(sub(c[3], cu), te) / le;
-      if (dist < rbar * len(g)) return false;
-    }
-    if (i > 0) {
-      const double ct = dot(ts, tu) / (ls * lu);
-      P4 g = axpy(-ct, P4{{tu.v[0] / lu, tu.v[1] / lu, tu.v[2] / lu, 0}},
-                  P4{{ts.v[0] / ls, ts.v[1] / ls, ts.v[2] / ls, 0}});
-      const double dist = dot(sub(cu, c[0]), ts) / ls;
-      if (dist < rbar * len(g)) return false;
-    }
+  Bern tj[3];  // t = c' / 3: Bernstein coefficients p1 - p0, p2 - p1, p3 - p2
+  for (int j = 0; j < 3; ++j) {
+    tj[j].n = 2;
+    for (int k = 0; k < 3; ++k) tj[j].b[k] = c[k + 1].v[j] - c[k].v[j];
   }
-  return rbar * curvature_at(c, 0.0) < 1.0 && rbar * curvature_at(c, 1.0) < 1.0;
+  Bern T;
+  T.n = 4;
+  for (int j = 0; j < 3; ++j) T = combine(T, 1.0, product(tj[j], tj[j]), 1.0);
+  for (int e = 0; e < 2; ++e) {
+    const P4 n = e == 0 ? sub(c[1], c[0]) : sub(c[3], c[2]);
+    const double nn = dot(n, n);
+    if (!(nn > 0.0)) return false;
+    Bern D, G;  // D = <c - p0, n> (start) or <p3 - c, n> (end); G = <n, t>
+    D.n = 3;
+    G.n = 2;
+    for (int k = 0; k < 4; ++k) D.b[k] = e == 0 ? dot(sub(c[k], c[0]), n) : dot(sub(c[3], c[k]), n);
+    for (int k = 0; k < 3; ++k) G.b[k] = n.v[0] * tj[0].b[k] + n.v[1] * tj[1].b[k] + n.v[2] * tj[2].b[k];
+    const Bern X = combine(T, nn, product(G, G), -1.0);  // |n x t|^2
+    const Bern P = combine(product(product(D, D), T), 1.0, X, -rbar * rbar);
+    const Bern E = e == 0 ? div_u(D) : div_one_minus_u(D);
+    const Bern Q = e == 0 ? div_u(div_u(P)) : div_one_minus_u(div_one_minus_u(P));
+    if (!nonneg01(E) || !nonneg01(Q)) return false;
+  }
+  return true;
 }
 
 // De Casteljau at u = 1/2.

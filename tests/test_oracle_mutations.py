@@ -14,7 +14,7 @@ import oracle as O
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_primitives.py", "tests/test_oracle_traversal.py",
         "tests/test_oracle_grad.py", "tests/test_oracle_normals.py", "tests/test_oracle_quadratic.py",
-        "tests/test_oracle_counts.py"]
+        "tests/test_oracle_counts.py", "tests/test_oracle_thick.py"]
 
 MUTATIONS = {
     "split_dp_coefficient": ("*dp = add4(add4(mul4(0.375, c->t0)", "*dp = add4(add4(mul4(0.125, c->t0)"),
@@ -49,6 +49,10 @@ MUTATIONS = {
     "normal_cap_points": ("int a = cap0 ? 0 : 3, b = cap0 ? 1 : 2;", "int a = cap0 ? 0 : 3, b = cap0 ? 1 : 1;"),
     "box_dilation_dropped": ("lo[a] = dmin(lo[a], v[a] - q[k].w);", "lo[a] = dmin(lo[a], v[a]);"),
     "box_retest_uncounted": ("        *count += 1;\n        if (box_hit(b, *best))", "        if (box_hit(b, *best))"),
+    "thick_drops_radius": ("poly_t Pq = padd(pmul(pmul(D, D), T), X, -rbar * rbar);",
+                           "poly_t Pq = padd(pmul(pmul(D, D), T), X, -rbar);"),
+    "thick_end_normal": ("v4 nrm[2] = {sub4(P[1], P[0]), sub4(P[3], P[2])};",
+                         "v4 nrm[2] = {sub4(P[1], P[0]), sub4(P[3], P[1])};"),
     "quadratic_elevation_weight": ("cp16[4 + a] = (p0 + 2.0 * p1) / 3.0;", "cp16[4 + a] = (2.0 * p0 + p1) / 3.0;"),
     "quadratic_constraint_sign": ("return dot3(a, b) <= 0.0;", "return dot3(a, b) >= 0.0;"),
     "normal_cap_plane_sign": ("cap0 = dot3(sub4(x, Q[0]), a0) / sqrt(dot3(a0, a0)) >= -tol;",
