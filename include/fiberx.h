@@ -266,14 +266,29 @@ fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray,
 /*
  * intersect_closest_host -- intersect_closest on HOST buffers: copies rays,
  * row_ptr and seg_idx to device staging owned by the handle, runs, copies
- * tu / seg / leaf back and synchronises.  Host buffers should be pinned for
- * full copy bandwidth.  Same flags and errors as intersect_closest, plus
- * FX_ENOMEM if the staging cannot grow.
+ * tu / seg / leaf back and synchronises.  Large calls are cut into up to 4
+ * chunks of rows with about equal input bytes; each chunk's copy in, kernels
+ * and copy out run on two copy streams owned by the handle and on `stream`,
+ * so copies overlap the other chunks' kernels (the naive kernel takes one
+ * chunk).  Rays are copied only in blocks of 8192 rows that hold a
+ * candidate (the ray of an empty row is never read; its result is a miss).
+ * Both rely on the CSR contract above (row_ptr[0] = 0, non-decreasing,
+ * row_ptr[n_ray] = n_pair).  Host buffers should be pinned
+ * for full copy bandwidth and asynchronous copies.  Calls on one handle must
+ * not overlap (they share its staging).  Same flags and errors as
+ * intersect_closest, plus FX_ENOMEM if the staging cannot grow.
  */
 fx_status intersect_closest_host(fx_fibers *f, const float *rays, int64_t n_ray,
                                  const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
                                  int32_t depth, uint32_t flags, float *tu, int32_t *seg,
                                  int32_t *leaf, void *stream);
+
+/*
+ * fx_host_bytes -- bytes the last intersect_closest_host call on this handle
+ * copied host to device (*h2d) and device to host (*d2h); 0 before the first
+ * call.  Errors: FX_EINVAL (null pointers).
+ */
+fx_status fx_host_bytes(const fx_fibers *f, int64_t *h2d, int64_t *d2h);
 
 /*
  * fx_set_launch / fx_get_launch -- launch shape of the persistent kernels of

@@ -328,6 +328,10 @@ void fiber_free(fx_fibers* f) {
   cudaFree(f->piece_root);
   cudaFree(f->ws);
   cudaFree(f->stage);
+  for (cudaEvent_t e : f->host_ev)
+    if (e) cudaEventDestroy(e);
+  if (f->copy_in) cudaStreamDestroy(f->copy_in);
+  if (f->copy_out) cudaStreamDestroy(f->copy_out);
   if (f->pool) cudaMemPoolDestroy(f->pool);  // released once its last allocation is freed
   delete f;
 }
@@ -460,23 +464,113 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
     if (cudaMalloc(&f->stage, need) != cudaSuccess) return fail(FX_ENOMEM, "staging allocation");
     f->stage_bytes = need;
   }
+  if (!f->copy_in) {
+    FX_CUDA(cudaStreamCreateWithFlags(&f->copy_in, cudaStreamNonBlocking));
+    FX_CUDA(cudaStreamCreateWithFlags(&f->copy_out, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : f->host_ev) FX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   char* base = (char*)f->stage;
   float* d_rays = (float*)base;
   int32_t* d_rp = (int32_t*)(base + b_rays);
   int32_t* d_si = (int32_t*)(base + b_rays + b_rp);
   float* d_tu = (float*)(base + b_rays + b_rp + b_si);
   int32_t* d_seg = (int32_t*)(base + b_rays + b_rp + b_si + b_tu);
-  int32_t* d_leaf = (int32_t*)(base + b_rays + b_rp + b_si + b_tu + b_seg);
-  FX_CUDA(cudaMemcpyAsync(d_rays, rays, (size_t)n_ray * 32, cudaMemcpyHostToDevice, s));
-  FX_CUDA(cudaMemcpyAsync(d_rp, row_ptr, (size_t)(n_ray + 1) * 4, cudaMemcpyHostToDevice, s));
-  if (n_pair > 0) FX_CUDA(cudaMemcpyAsync(d_si, seg_idx, (size_t)n_pair * 4, cudaMemcpyHostToDevice, s));
-  st = intersect_closest(f, d_rays, n_ray, d_rp, d_si, n_pair, depth, flags, d_tu, d_seg,
-                         (leaf || (flags & FX_POLISH_FP64)) ? d_leaf : nullptr, stream);
+  int32_t* d_leaf = (leaf || (flags & FX_POLISH_FP64)) ? (int32_t*)(base + b_rays + b_rp + b_si + b_tu + b_seg)
+                                                       : nullptr;
+
+  // Rows are cut into up to kFxHostChunks chunks of about equal input bytes
+  // (32 per ray, 4 per row_ptr entry, 4 per pair), found by bisection on the
+  // host row_ptr.  Chunk c is copied in on copy_in, intersected on the
+  // caller's stream once its copy is done, and its results copied out on
+  // copy_out, so copies overlap the other chunks' kernels.  Each chunk's
+  // kernels read the CSR in place (row_ptr values index the whole seg_idx
+  // staging), and the copies run in row order, so a chunk's pairs have
+  // arrived with it.  No kernel reads the ray of an empty row, so rays are
+  // copied only in blocks of kRayBlock rows that hold a candidate, one copy
+  // per run of such blocks.  The pair-parallel naive kernel indexes pairs of
+  // the whole CSR: one chunk.
+  constexpr int64_t kChunkBytes = 32 << 20;
+  constexpr int64_t kRayBlock = 8192;
+  const int64_t in_bytes = 36 * n_ray + 4 * n_pair;
+  int n_chunk = (int)std::min<int64_t>(kFxHostChunks, std::max<int64_t>(1, in_bytes / kChunkBytes));
+  if (flags & FX_KERNEL_NAIVE) n_chunk = 1;
+  auto pairs_at = [&](int64_t r) { return std::min<int64_t>(std::max<int32_t>(row_ptr[r], 0), n_pair); };
+  int64_t cut[kFxHostChunks + 1];
+  cut[0] = 0;
+  cut[n_chunk] = n_ray;
+  for (int c = 1; c < n_chunk; ++c) {
+    const int64_t target = in_bytes * c / n_chunk;
+    int64_t lo = cut[c - 1], hi = n_ray;  // smallest r in [lo, hi] with bytes(r) >= target
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (36 * mid + 4 * pairs_at(mid) >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    cut[c] = lo;
+  }
+
+  cudaEvent_t* ev_in = f->host_ev + 1;
+  cudaEvent_t* ev_done = f->host_ev + 1 + kFxHostChunks;
+  cudaError_t e = cudaEventRecord(f->host_ev[0], s);  // work queued on the caller's stream comes first
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_in, f->host_ev[0], 0);
+  int64_t p_done = 0;
+  f->host_h2d = f->host_d2h = 0;
+  auto empty_block = [&](int64_t b, int64_t b_end) { return pairs_at(b) == pairs_at(b_end); };
+  for (int c = 0; c < n_chunk && e == cudaSuccess && st == FX_OK; ++c) {
+    const int64_t r0 = cut[c], r1 = cut[c + 1], n = r1 - r0;
+    const int64_t p1 = c + 1 == n_chunk ? n_pair : std::max(p_done, pairs_at(r1));
+    for (int64_t b = r0; b < r1 && e == cudaSuccess;) {
+      int64_t run_end = std::min(b + kRayBlock, r1);
+      if (empty_block(b, run_end)) {
+        b = run_end;
+        continue;
+      }
+      while (run_end < r1 && !empty_block(run_end, std::min(run_end + kRayBlock, r1)))
+        run_end = std::min(run_end + kRayBlock, r1);
+      e = cudaMemcpyAsync(d_rays + 8 * b, rays + 8 * b, (size_t)(run_end - b) * 32, cudaMemcpyHostToDevice,
+                          f->copy_in);
+      f->host_h2d += (run_end - b) * 32;
+      b = run_end;
+    }
+    f->host_h2d += (n + 1) * 4 + (p1 - p_done) * 4;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_rp + r0, row_ptr + r0, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, f->copy_in);
+    if (e == cudaSuccess && p1 > p_done)
+      e = cudaMemcpyAsync(d_si + p_done, seg_idx + p_done, (size_t)(p1 - p_done) * 4, cudaMemcpyHostToDevice,
+                          f->copy_in);
+    p_done = p1;
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], f->copy_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[c], 0);
+    if (e != cudaSuccess || n == 0) continue;
+    st = intersect_closest(f, d_rays + 8 * r0, n, d_rp + r0, d_si, n_pair, depth, flags, d_tu + 2 * r0, d_seg + r0,
+                           d_leaf ? d_leaf + r0 : nullptr, stream);
+    if (st != FX_OK) break;
+    e = cudaEventRecord(ev_done[c], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_out, ev_done[c], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tu + 2 * r0, d_tu + 2 * r0, (size_t)n * 8, cudaMemcpyDeviceToHost, f->copy_out);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(seg + r0, d_seg + r0, (size_t)n * 4, cudaMemcpyDeviceToHost, f->copy_out);
+    if (e == cudaSuccess && leaf)
+      e = cudaMemcpyAsync(leaf + r0, d_leaf + r0, (size_t)n * 4, cudaMemcpyDeviceToHost, f->copy_out);
+    f->host_d2h += n * (leaf ? 16 : 12);
+  }
+  // nothing of this call may still touch the caller's buffers on return
+  const cudaError_t e_in = cudaStreamSynchronize(f->copy_in);
+  const cudaError_t e_s = cudaStreamSynchronize(s);
+  const cudaError_t e_out = cudaStreamSynchronize(f->copy_out);
   if (st != FX_OK) return st;
-  FX_CUDA(cudaMemcpyAsync(tu, d_tu, (size_t)n_ray * 8, cudaMemcpyDeviceToHost, s));
-  FX_CUDA(cudaMemcpyAsync(seg, d_seg, (size_t)n_ray * 4, cudaMemcpyDeviceToHost, s));
-  if (leaf) FX_CUDA(cudaMemcpyAsync(leaf, d_leaf, (size_t)n_ray * 4, cudaMemcpyDeviceToHost, s));
-  FX_CUDA(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) return cuda_fail(e, "host-buffer pipeline");
+  if (e_in != cudaSuccess) return cuda_fail(e_in, "copy-in stream");
+  if (e_s != cudaSuccess) return cuda_fail(e_s, "intersect stream");
+  if (e_out != cudaSuccess) return cuda_fail(e_out, "copy-out stream");
+  return FX_OK;
+}
+
+fx_status fx_host_bytes(const fx_fibers* f, int64_t* h2d, int64_t* d2h) {
+  if (!f || !h2d || !d2h) return fail(FX_EINVAL, "null argument");
+  *h2d = f->host_h2d;
+  *d2h = f->host_d2h;
   return FX_OK;
 }
 

@@ -15,6 +15,9 @@ enum {
   FX_WS_WORDS = 32,   // 128 bytes of uint32 words, then the counters
 };
 
+// chunks of the host-buffer entry's copy / compute pipeline
+constexpr int kFxHostChunks = 4;
+
 struct fx_fibers {
   int device = 0;
   int sm_count = 0;
@@ -32,9 +35,13 @@ struct fx_fibers {
   // stream-ordered scratch of the intersect calls; keeps its memory between
   // calls (release threshold: never), so repeated calls do not remap it
   cudaMemPool_t pool = nullptr;
-  // host-buffer entry staging (grow-only)
+  // host-buffer entry staging (grow-only), its copy streams and the events
+  // that order its chunks (created on first use)
   void *stage = nullptr;
   size_t stage_bytes = 0;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t host_ev[1 + 2 * kFxHostChunks] = {};
+  int64_t host_h2d = 0, host_d2h = 0;  // bytes the last host-buffer call copied
 };
 
 namespace fx {

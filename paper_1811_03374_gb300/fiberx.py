@@ -40,7 +40,8 @@ FX_VARIANT_RAY = 5
 
 MAX_DEPTH = 23
 EXPORTS = ["fiber_upload", "fiber_upload_quadratic", "fiber_free", "fiber_info", "intersect_closest", "intersect_pairs",
-           "intersect_backward", "intersect_normals", "intersect_counts", "intersect_closest_host", "intersect_closest_noalloc",
+           "intersect_backward", "intersect_normals", "intersect_counts", "intersect_closest_host", "fx_host_bytes",
+           "intersect_closest_noalloc",
            "fx_set_launch",
            "fx_get_launch", "fx_counters", "fx_stream_status", "fx_fma_peak", "fx_last_error", "fx_version"]
 NOALLOC_MAX_RAYS = 1 << 20
@@ -107,6 +108,8 @@ def lib():
             L.intersect_normals.restype = i32
             L.intersect_closest_host.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
             L.intersect_closest_host.restype = i32
+            L.fx_host_bytes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+            L.fx_host_bytes.restype = i32
             L.intersect_closest_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
             L.intersect_closest_noalloc.restype = i32
             L.fx_set_launch.argtypes = [vp, ctypes.POINTER(Launch)]
@@ -356,6 +359,14 @@ def intersect_closest_host(fibers, rays, row_ptr, seg_idx, depth, flags=0, out=N
                                         n_pair, int(depth), int(flags), _ptr(tu), _ptr(seg), _ptr(lf),
                                         _stream(stream)))
     return tu, seg, lf
+
+
+def host_bytes(fibers):
+    """(h2d, d2h): bytes the last intersect_closest_host call on ``fibers``
+    copied each way."""
+    h2d, d2h = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().fx_host_bytes(fibers.handle, ctypes.byref(h2d), ctypes.byref(d2h)))
+    return int(h2d.value), int(d2h.value)
 
 
 def _autograd():

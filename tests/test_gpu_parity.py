@@ -339,6 +339,58 @@ def test_host_entry_matches_device(tiny):
     fib.close()
 
 
+def _chunked_case():
+    """About 90 MB of host input, so the host entry cuts it into chunks:
+    1M rays over 65,536 segments, each ray's own segment among 15 random
+    others, every seventh row empty, rows 100,000-299,999 and 900,001-end
+    empty (whole blocks of rays are then not copied), and one row of 300,000
+    candidates."""
+    base = I.sweep_case("moderate", 65536, forced_hits=True)
+    g = np.random.default_rng(41)
+    n_ray = 1 << 20
+    rays = np.tile(base["rays"], (16, 1))
+    own = np.tile(np.arange(65536, dtype=np.int32), 16)
+    lens = np.full(n_ray, 16, np.int64)
+    lens[::7] = 0
+    lens[100_000:300_000] = 0
+    lens[900_001:] = 0
+    lens[500_001] = 300_000
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    seg_idx = g.integers(0, 65536, int(row_ptr[-1])).astype(np.int32)
+    first = row_ptr[:-1][lens > 0]
+    seg_idx[first + g.integers(0, 16, len(first))] = own[lens > 0]
+    return dict(cps=base["cps"], rays=rays, row_ptr=row_ptr, seg_idx=seg_idx)
+
+
+@pytest.mark.parametrize("variant,flags", [(F.FX_VARIANT_LANE, 0), (F.FX_VARIANT_SCAN, F.FX_FAST_MATH),
+                                           (F.FX_VARIANT_LANE, F.FX_POLISH_FP64),
+                                           (F.FX_VARIANT_LANE, F.FX_KERNEL_NAIVE)],
+                         ids=["lane", "scan-fast", "lane-polish", "naive"])
+def test_host_entry_pipeline_matches_device(variant, flags):
+    # the chunked copy / compute pipeline of the host entry gives the device
+    # entry's results bit for bit
+    case = _chunked_case()
+    fib = F.Fibers(case["cps"])
+    fib.set_launch(variant=variant)
+    tu_d, seg_d, leaf_d = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 12, flags)
+    torch.cuda.synchronize()
+    h = tuple(torch.from_numpy(np.asarray(x)).pin_memory() for x in (case["rays"], case["row_ptr"], case["seg_idx"]))
+    for _ in range(2):  # the second call reuses the staging and the streams
+        tu_h, seg_h, leaf_h = F.intersect_closest_host(fib, *h, 12, flags)
+        np.testing.assert_array_equal(_np(tu_d), tu_h.numpy())
+        np.testing.assert_array_equal(_np(seg_d), seg_h.numpy())
+        np.testing.assert_array_equal(_np(leaf_d), leaf_h.numpy())
+        h2d, d2h = F.host_bytes(fib)
+        n_ray, n_pair = len(case["rays"]), len(case["seg_idx"])
+        assert d2h == 16 * n_ray
+        # the two empty ranges hold at least 36 whole blocks of 8192 rays at any
+        # block alignment: their rays stay behind
+        assert 4 * (n_ray + 1) + 4 * n_pair < h2d <= 32 * n_ray + 4 * (n_ray + 4) + 4 * n_pair - 36 * 8192 * 32
+    assert (seg_h.numpy() >= 0).sum() > 400_000
+    assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
+    fib.close()
+
+
 @pytest.mark.parametrize("variant", [F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN, F.FX_VARIANT_RAY],
                          ids=["lane", "scan", "ray"])
 def test_edge_cases(variant):
