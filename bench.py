@@ -267,7 +267,9 @@ def main():
 
     case = load_workload(rank)
     n_ray, n_pair = case["rays"].shape[0], len(case["seg_idx"])
-    fib = F.Fibers(case["cps"])
+    t_up = time.perf_counter()
+    fib = F.Fibers(case["cps"])  # host FP64 validation and pre-split, one copy per array (untimed)
+    upload_s = time.perf_counter() - t_up
     info = fib.info()
     rays = torch.from_numpy(case["rays"]).to(dev)
     row_ptr = torch.from_numpy(case["row_ptr"]).to(dev)
@@ -299,6 +301,7 @@ def main():
     n_ray_cand = int(np.count_nonzero(np.diff(case["row_ptr"])))
     n_piece_touched = int(len(np.unique(case["seg_idx"])))
     work = FL.alg_flops(counters, n_ray_cand)
+    mwork = FL.method_flops(counters, n_ray_cand)
     abytes = FL.alg_bytes(n_ray, n_pair, n_piece_touched)
 
     graph = None
@@ -390,6 +393,10 @@ def main():
                 "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)" % sm,
                 "fma_microbenchmark_tflops": fma_tflops,
                 "alg_flops_per_launch": work,
+                # context: the paper's algorithm on the same frame (no bound
+                # test; every candidate set up and its root tested), at this time
+                "method_flops_per_launch": mwork,
+                "frac_method_equivalent": mwork / (ms_step * 1e-3) / 1e12 / peak,
                 "hbm_gbs_algorithmic": abytes / (ms_step * 1e-3) / 1e9,
                 "alg_bytes_per_launch": abytes}
     if clk:
@@ -414,7 +421,8 @@ def main():
                      "launch": fib.get_launch(), "cuda_graph": graph is not None,
                      "l2": "flushed between timed steps (256 MB write)",
                      "parallelism": "replica per GPU" if world > 1 else "single GPU",
-                     "counters": counters, "device_status": status, "timed_wall_s": wall},
+                     "counters": counters, "device_status": status, "timed_wall_s": wall,
+                     "fiber_upload_ms": upload_s * 1e3},
           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
           "gpu_launches": launches_per_step * args.steps, "clocks": clk}, args)
     fib.close()

@@ -17,6 +17,17 @@ totals are lower bounds.
   per backtrack    power-form recomputation (142) + slab (15)            157
   per hit          u by projection onto the leaf axis, segment mapping    17
 
+The paper's algorithm performs more for the same frame: it has no bound
+test, so every candidate pays the setup of Sec. 3.1 / 3.3 and a root node
+test like any node (method_flops):
+
+  per candidate    four control points into the ray frame (4 x 18),
+                   (p, d, t0, t1) differences (12), end-plane slab (15)   99
+                   + root node test as a deeper node                      68
+
+Descents, backtracks and hits are the same events on both: the bound test
+only removes root tests that cannot pass.
+
 Counters (all variants): tests = candidate pieces examined, nodes = node
 tests including roots, descents, backtracks, hits.  Every deeper node test
 follows a descent or a backtrack, so root node tests = nodes - descents -
@@ -30,6 +41,8 @@ PER_NODE = 68
 PER_DESCENT = 49
 PER_BACKTRACK = 157
 PER_HIT = 17
+
+PER_SETUP_METHOD = 99
 
 # Bytes a closest-hit launch must move at least once: ray (32 B) and two
 # row_ptr words per ray, one seg_idx word per pair, 64 B per piece touched,
@@ -45,6 +58,15 @@ def alg_flops(counters, n_ray_with_candidates):
     return (PER_RAY * n_ray_with_candidates + PER_BOUND * c["tests"] + PER_ROOT * (c["nodes"] - deeper)
             + PER_NODE * deeper + PER_DESCENT * c["descents"] + PER_BACKTRACK * c["backtracks"]
             + PER_HIT * c["hits"])
+
+
+def method_flops(counters, n_ray_with_candidates):
+    """The paper's algorithm on the same frame: every candidate set up and
+    its root tested as a node, then the same descents, backtracks and hits."""
+    c = counters
+    deeper = c["descents"] + c["backtracks"]
+    return (PER_RAY * n_ray_with_candidates + (PER_SETUP_METHOD + PER_NODE) * c["tests"] + PER_NODE * deeper
+            + PER_DESCENT * c["descents"] + PER_BACKTRACK * c["backtracks"] + PER_HIT * c["hits"])
 
 
 def alg_bytes(n_ray, n_pair, n_piece_touched):
