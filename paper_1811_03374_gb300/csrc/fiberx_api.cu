@@ -489,8 +489,14 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   // copied only in blocks of kRayBlock rows that hold a candidate, one copy
   // per run of such blocks.  The pair-parallel naive kernel indexes pairs of
   // the whole CSR: one chunk.
-  constexpr int64_t kChunkBytes = 32 << 20;
-  constexpr int64_t kRayBlock = 8192;
+#ifndef FX_HOST_CHUNK_MB
+#define FX_HOST_CHUNK_MB 32
+#endif
+#ifndef FX_HOST_RAY_BLOCK
+#define FX_HOST_RAY_BLOCK 8192
+#endif
+  constexpr int64_t kChunkBytes = (int64_t)FX_HOST_CHUNK_MB << 20;
+  constexpr int64_t kRayBlock = FX_HOST_RAY_BLOCK;
   const int64_t in_bytes = 36 * n_ray + 4 * n_pair;
   int n_chunk = (int)std::min<int64_t>(kFxHostChunks, std::max<int64_t>(1, in_bytes / kChunkBytes));
   if (flags & FX_KERNEL_NAIVE) n_chunk = 1;

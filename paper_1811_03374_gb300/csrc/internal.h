@@ -15,8 +15,11 @@ enum {
   FX_WS_WORDS = 32,   // 128 bytes of uint32 words, then the counters
 };
 
-// chunks of the host-buffer entry's copy / compute pipeline
-constexpr int kFxHostChunks = 4;
+// chunks of the host-buffer entry's copy / compute pipeline (at most)
+#ifndef FX_HOST_CHUNKS
+#define FX_HOST_CHUNKS 4
+#endif
+constexpr int kFxHostChunks = FX_HOST_CHUNKS;
 
 struct fx_fibers {
   int device = 0;
