@@ -117,7 +117,20 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
   if (variant == FX_VARIANT_WARP) {
     FX_CUDA(fx::launch_warp_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
   } else if (variant == FX_VARIANT_RAY) {
-    FX_CUDA(fx::launch_ray(a, pairs, flags, s));
+    // closest hits: room for a walk per ray that the first pass may leave to
+    // the second (128 bytes each, from the pool; only the saved ones are
+    // written), the count in the first 256 bytes
+    fx::RayDefer d{nullptr, nullptr, 0};
+    char* buf = nullptr;
+    if (!pairs) {
+      const uint32_t cap = (uint32_t)a.n_ray;
+      FX_CUDA(cudaMallocFromPoolAsync((void**)&buf, 256 + fx::ray_walk_bytes() * cap, f->pool, s));
+      d = fx::RayDefer{buf + 256, reinterpret_cast<uint32_t*>(buf), cap};
+    }
+    cudaError_t e = buf ? cudaMemsetAsync(buf, 0, sizeof(uint32_t), s) : cudaSuccess;
+    if (e == cudaSuccess) e = fx::launch_ray(a, pairs, flags, d, f->sm_count, s);
+    if (buf) cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return cuda_fail(e, "per-ray kernels");
   } else if (variant == FX_VARIANT_SCAN) {
     int4* act = nullptr;
     FX_CUDA(cudaMallocFromPoolAsync((void**)&act, sizeof(int4) * (size_t)(a.n_ray + 1), f->pool, s));

@@ -111,7 +111,16 @@ cudaError_t launch_scan_ray(const TraceArgs &a, const ScanArgs &o, bool pairs, u
                             int blocks_per_sm_cap, int sm_count, cudaStream_t s);
 
 // ray_kernels.cu: one thread per ray (handles with single level-0 pieces only)
-cudaError_t launch_ray(const TraceArgs &a, bool pairs, uint32_t flags, cudaStream_t s);
+// Walks the per-ray variant's first pass leaves to its second (closest
+// hits; null walks: one pass).  A walk is ray_walk_bytes() (128) bytes.
+struct RayDefer {
+  void *walks;        // capacity saved walks, 16-byte aligned
+  uint32_t *count;    // zeroed before the first pass
+  uint32_t capacity;  // walks the list holds: one per ray
+};
+size_t ray_walk_bytes();
+cudaError_t launch_ray(const TraceArgs &a, bool pairs, uint32_t flags, const RayDefer &d, int sm_count,
+                       cudaStream_t s);
 
 // warp_kernels.cu
 cudaError_t launch_warp_ray(const TraceArgs &a, bool pairs, uint32_t flags, int blocks_per_sm_cap,

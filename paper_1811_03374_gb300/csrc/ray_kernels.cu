@@ -12,6 +12,15 @@
 // with one candidate per ray the persistent kernels' machinery costs more
 // than the traversal.  Handles whose segments are single level-0 pieces
 // only; others run the lane kernel.
+//
+// Closest hits take two passes.  The first gives each ray a budget of node
+// tests.  A ray done within it (most rays against a single fiber miss at the
+// root) is finished there; a ray that needs more saves its walk -- the node
+// about to be tested, the bit string, the slab, the closest hit so far, the
+// candidate -- to a list, and the second pass continues it from there.  The
+// few rays with long traversals thus no longer hold warps of rays with short
+// ones, and no node test is done twice.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -25,6 +34,29 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRayBlock = 128;
 // relative slack of the bound test against FP32 rounding (the lane kernel's)
 constexpr float kBoundSlack = 1.0f / 262144.0f;
+// node tests a ray may take in the first pass of closest hits
+#ifndef FX_RAY_BUDGET
+#define FX_RAY_BUDGET 4
+#endif
+constexpr int kBudget = FX_RAY_BUDGET;
+static_assert(kBudget >= 1, "the first pass takes at least the root test");
+
+// Walk modes: the whole walk in one pass (closest hits or per pair); the
+// first pass of closest hits (at most kBudget node tests, then the walk is
+// saved); the second pass (continues a saved walk).
+enum WalkMode { kWalkAll = 0, kWalkFirst = 1, kWalkResume = 2 };
+
+// A closest-hit walk saved between the passes (128 bytes).
+struct alignas(16) RayWalk {
+  Node c;                     // the node about to be tested, ray frame
+  float tmin, tmax, root_r, best_t;
+  float best_u;
+  int32_t ray, j, best_seg;   // ray, current candidate, closest hit's segment
+  int32_t best_leaf, iters;
+  uint32_t bits, start;
+  uint32_t size, slab_ok, pad0, pad1;
+};
+static_assert(sizeof(RayWalk) == 128, "two cache sectors per saved walk");
 
 __device__ __forceinline__ void rotate_piece(const float4* __restrict__ piece, int32_t k, const RayFrame& r,
                                              Node& n) {
@@ -36,28 +68,73 @@ __device__ __forceinline__ void rotate_piece(const float4* __restrict__ piece, i
   n.t1 = rotate(r, t1.x, t1.y, t1.z, t1.w);
 }
 
-template <bool FAST, bool PAIRS, bool COUNT>
-__global__ void __launch_bounds__(kRayBlock) k_ray(const TraceArgs a, int check) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Ray r against its candidates.  kWalkFirst returns true when the ray needs
+// more than kBudget node tests: `w` then holds its walk, nothing is written,
+// and the events so far are counted.  kWalkResume continues the walk in `w`.
+// Otherwise the ray's result is written and it returns false.
+template <bool FAST, bool PAIRS, bool COUNT, int MODE>
+__device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk& w, int check,
+                                         uint32_t (&cnt)[5]) {
+  static_assert(MODE == kWalkAll || !PAIRS, "the two passes serve closest hits");
   uint32_t n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
-  if (r < a.n_ray) {
-    const int32_t crow = __ldg(a.row_ptr + r), cend = __ldg(a.row_ptr + r + 1);
-    float ray_tmax = 0.0f, best_t = 0.0f, best_u = -1.0f;
-    int32_t best_seg = -1, best_leaf = -1;
-    RayFrame rf{};
-    if (crow < cend) {
-      rf = load_ray<FAST>(a.rays, r, ray_tmax);
-      best_t = ray_tmax;
+  auto flush = [&]() {
+    if (COUNT) {
+      cnt[0] += n_nodes;
+      cnt[1] += n_desc;
+      cnt[2] += n_back;
+      cnt[3] += n_tests;
+      cnt[4] += n_hits;
     }
-    const int min_size = 1 << piece_min_size_shift(a.depth, 0);
-    for (int32_t j = crow; j < cend; ++j) {
-      const int32_t s = __ldg(a.seg_idx + j);
-      float cand_t = ray_tmax, cand_u = -1.0f;
-      int32_t cand_leaf = -1;
-      const float lim = PAIRS ? ray_tmax : best_t;
-      bool test = s >= 0 && (!check || s < a.n_seg);
+  };
+  const int32_t crow = __ldg(a.row_ptr + r), cend = __ldg(a.row_ptr + r + 1);
+  float ray_tmax = 0.0f, best_t = 0.0f, best_u = -1.0f;
+  int32_t best_seg = -1, best_leaf = -1;
+  RayFrame rf{};
+  if (crow < cend) {
+    rf = load_ray<FAST>(a.rays, r, ray_tmax);
+    best_t = ray_tmax;
+  }
+  int32_t j = crow;
+  bool resume = false;
+  if (MODE == kWalkResume) {
+    best_t = w.best_t;
+    best_u = w.best_u;
+    best_seg = w.best_seg;
+    best_leaf = w.best_leaf;
+    j = w.j;
+    resume = true;
+  }
+  const int min_size = 1 << piece_min_size_shift(a.depth, 0);
+  int used = 0;  // node tests of this pass (kWalkFirst's budget)
+  for (; j < cend; ++j) {
+    const int32_t s = __ldg(a.seg_idx + j);
+    float cand_t = ray_tmax, cand_u = -1.0f;
+    int32_t cand_leaf = -1;
+    const float lim = PAIRS ? ray_tmax : best_t;
+    Node R, c;
+    float tmin = 0.0f, tmax = lim, root_r = 0.0f;
+    uint32_t bits = 0, start = 0, size = kRootSize;
+    bool slab_ok = false;
+    int iters = 0;
+    bool test;
+    if (MODE == kWalkResume && resume) {
+      // the saved walk of this candidate; its root is rebuilt by the same
+      // arithmetic as when the first pass began it
+      resume = false;
+      rotate_piece(a.piece, s, rf, R);
+      c = w.c;
+      tmin = w.tmin;
+      tmax = w.tmax;
+      root_r = w.root_r;
+      bits = w.bits;
+      start = w.start;
+      size = w.size;
+      slab_ok = w.slab_ok != 0u;
+      iters = w.iters;
+      test = true;
+    } else {
+      test = s >= 0 && (!check || s < a.n_seg);
       if (!test) atomicOr(a.status, FX_DEV_BAD_INDEX);
-      float root_r = 0.0f;
       if (test) {
         // bound test on the root record: the sphere that holds the root
         // node's capped cylinder lies beyond t_max
@@ -71,103 +148,207 @@ __global__ void __launch_bounds__(kRayBlock) k_ray(const TraceArgs a, int check)
         root_r = P.w;
       }
       if (test) {
-        Node R, c;
         rotate_piece(a.piece, s, rf, R);
         c = R;
-        float tmin = 0.0f, tmax = lim;
-        uint32_t bits = 0, start = 0, size = kRootSize;
-        bool slab_ok = false;
-        for (int iters = 0;;) {
-          const float pair_tmax = PAIRS ? cand_t : best_t;
-          const float rad = (iters == 0) ? root_r : cons_radius<FAST>(c);
-          float c0 = 0.0f, c1 = 0.0f;
-          bool over = cylinder<FAST>(c.p, c.d, rad, c0, c1);
-          if (over && !slab_ok) {
-            const float l = tmax;
-            slab<FAST>(c, l, tmin, tmax);
-            slab_ok = true;
+      }
+    }
+    if (test) {
+      for (;;) {
+        if (MODE == kWalkFirst) {
+          if (used == kBudget) {  // save the walk for the second pass
+            w.c = c;
+            w.tmin = tmin;
+            w.tmax = tmax;
+            w.root_r = root_r;
+            w.best_t = best_t;
+            w.best_u = best_u;
+            w.ray = (int32_t)r;
+            w.j = j;
+            w.best_seg = best_seg;
+            w.best_leaf = best_leaf;
+            w.iters = iters;
+            w.bits = bits;
+            w.start = start;
+            w.size = size;
+            w.slab_ok = slab_ok ? 1u : 0u;
+            flush();
+            return true;
           }
-          over = over && fmaxf(c0, tmin) <= fminf(c1, tmax);
-          ++iters;
-          if (COUNT) ++n_nodes;
-          if (over && size <= (uint32_t)min_size) {
-            const float t = fmaxf(c0, tmin);
-            if (t < pair_tmax) {
-              float u;
-              int32_t lf;
-              to_segment(0, leaf_u<FAST>(c, t, start, size), start, u, lf);
-              if (PAIRS) {
-                cand_t = t;
-                cand_u = u;
-                cand_leaf = lf;
-              } else {
-                best_t = t;
-                best_u = u;
-                best_seg = s;
-                best_leaf = lf;
-              }
-              if (COUNT) ++n_hits;
+          ++used;
+        }
+        const float pair_tmax = PAIRS ? cand_t : best_t;
+        const float rad = (iters == 0) ? root_r : cons_radius<FAST>(c);
+        float c0 = 0.0f, c1 = 0.0f;
+        bool over = cylinder<FAST>(c.p, c.d, rad, c0, c1);
+        if (over && !slab_ok) {
+          const float l = tmax;
+          slab<FAST>(c, l, tmin, tmax);
+          slab_ok = true;
+        }
+        over = over && fmaxf(c0, tmin) <= fminf(c1, tmax);
+        ++iters;
+        if (COUNT) ++n_nodes;
+        if (over && size <= (uint32_t)min_size) {
+          const float t = fmaxf(c0, tmin);
+          if (t < pair_tmax) {
+            float u;
+            int32_t lf;
+            to_segment(0, leaf_u<FAST>(c, t, start, size), start, u, lf);
+            if (PAIRS) {
+              cand_t = t;
+              cand_u = u;
+              cand_leaf = lf;
+            } else {
+              best_t = t;
+              best_u = u;
+              best_seg = s;
+              best_leaf = lf;
             }
-            break;
-          } else if (over) {
-            descend<FAST>(c, c0, c1, tmin, tmax, bits, start, size);
-            if (COUNT) ++n_desc;
-          } else if (bits == 0u) {
-            break;
-          } else {
-            jump_up(bits, start, size);
-            recompute(R, start, size, c);
-            tmax = pair_tmax;
-            slab_ok = false;
-            if (COUNT) ++n_back;
+            if (COUNT) ++n_hits;
           }
-          if (iters >= iter_cap(a.depth)) {
-            atomicOr(a.status, FX_DEV_ITER_LIMIT);
-            break;
-          }
+          break;
+        } else if (over) {
+          descend<FAST>(c, c0, c1, tmin, tmax, bits, start, size);
+          if (COUNT) ++n_desc;
+        } else if (bits == 0u) {
+          break;
+        } else {
+          jump_up(bits, start, size);
+          recompute(R, start, size, c);
+          tmax = pair_tmax;
+          slab_ok = false;
+          if (COUNT) ++n_back;
+        }
+        if (iters >= iter_cap(a.depth)) {
+          atomicOr(a.status, FX_DEV_ITER_LIMIT);
+          break;
         }
       }
-      if (PAIRS) {
-        a.tu[j] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
-        if (a.leaf) a.leaf[j] = cand_leaf;
-      }
     }
-    if (!PAIRS) {
-      const bool hit = best_seg >= 0;
-      a.tu[r] = make_float2(hit ? best_t : kInf, hit ? best_u : -1.0f);
-      a.seg[r] = best_seg;
-      if (a.leaf) a.leaf[r] = best_leaf;
+    if (PAIRS) {
+      a.tu[j] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
+      if (a.leaf) a.leaf[j] = cand_leaf;
     }
   }
-  if (COUNT) {
-    unsigned long long v[5] = {n_nodes, n_desc, n_back, n_tests, n_hits};
-    for (int k = 0; k < 5; ++k) {
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(kFull, v[k], o);
-      if ((threadIdx.x & 31) == 0 && v[k]) atomicAdd(a.counters + k, v[k]);
-    }
+  if (!PAIRS) {
+    const bool hit = best_seg >= 0;
+    a.tu[r] = make_float2(hit ? best_t : kInf, hit ? best_u : -1.0f);
+    a.seg[r] = best_seg;
+    if (a.leaf) a.leaf[r] = best_leaf;
+  }
+  flush();
+  return false;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void add_counts(const TraceArgs& a, const uint32_t (&cnt)[5]) {
+  if (!COUNT) return;
+  unsigned long long v[5] = {cnt[0], cnt[1], cnt[2], cnt[3], cnt[4]};
+  for (int k = 0; k < 5; ++k) {
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(kFull, v[k], o);
+    if ((threadIdx.x & 31) == 0 && v[k]) atomicAdd(a.counters + k, v[k]);
   }
 }
 
+__device__ __forceinline__ void store_walk(RayWalk* dst, const RayWalk& w) {
+  const float4* src = reinterpret_cast<const float4*>(&w);
+  float4* out = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out[k] = src[k];
+}
+
+__device__ __forceinline__ void load_walk(const RayWalk* src, RayWalk& w) {
+  const float4* in = reinterpret_cast<const float4*>(src);
+  float4* dst = reinterpret_cast<float4*>(&w);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dst[k] = __ldg(in + k);
+}
+
+// One thread per ray, the whole walk (per-pair results, or closest hits in
+// one pass).
 template <bool FAST, bool PAIRS, bool COUNT>
-cudaError_t launch_r(const TraceArgs& a, int check, cudaStream_t s) {
+__global__ void __launch_bounds__(kRayBlock) k_ray(const TraceArgs a, int check) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t cnt[5] = {0, 0, 0, 0, 0};
+  RayWalk w;
+  if (r < a.n_ray) ray_walk<FAST, PAIRS, COUNT, kWalkAll>(a, r, w, check, cnt);
+  add_counts<COUNT>(a, cnt);
+}
+
+// First pass of closest hits.  A ray that runs out of budget takes a slot of
+// the list (one atomic per warp; the list has a slot for every ray).
+template <bool FAST, bool COUNT>
+__global__ void __launch_bounds__(kRayBlock) k_ray_first(const TraceArgs a, int check, RayDefer d) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t cnt[5] = {0, 0, 0, 0, 0};
+  RayWalk w;
+  bool defer = false;
+  if (r < a.n_ray) defer = ray_walk<FAST, false, COUNT, kWalkFirst>(a, r, w, check, cnt);
+  const unsigned m = __ballot_sync(kFull, defer);
+  if (m) {
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    uint32_t off = 0;
+    if (lane == lead) off = atomicAdd(d.count, (uint32_t)__popc(m));
+    off = __shfl_sync(kFull, off, lead);
+    const uint32_t slot = off + __popc(m & ((1u << lane) - 1u));
+    if (defer && slot < d.capacity) store_walk(reinterpret_cast<RayWalk*>(d.walks) + slot, w);
+  }
+  add_counts<COUNT>(a, cnt);
+}
+
+// Second pass: the saved walks, one thread each, grid-stride over the list.
+template <bool FAST, bool COUNT>
+__global__ void __launch_bounds__(kRayBlock) k_ray_resume(const TraceArgs a, int check, RayDefer d) {
+  const uint32_t n = min(*d.count, d.capacity);
+  uint32_t cnt[5] = {0, 0, 0, 0, 0};
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // a warp-uniform trip count, so that the counters' shuffles see full warps
+  const uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+  for (uint32_t i0 = base; i0 < n; i0 += stride) {
+    const uint32_t i = i0 + (threadIdx.x & 31);
+    if (i < n) {
+      RayWalk w;
+      load_walk(reinterpret_cast<const RayWalk*>(d.walks) + i, w);
+      ray_walk<FAST, false, COUNT, kWalkResume>(a, w.ray, w, check, cnt);
+    }
+  }
+  add_counts<COUNT>(a, cnt);
+}
+
+template <bool FAST, bool PAIRS, bool COUNT>
+cudaError_t launch_r(const TraceArgs& a, int check, const RayDefer& d, int sms, cudaStream_t s) {
   const int64_t grid = (a.n_ray + kRayBlock - 1) / kRayBlock;
-  k_ray<FAST, PAIRS, COUNT><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check);
+  if (PAIRS || !d.walks) {
+    k_ray<FAST, PAIRS, COUNT><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check);
+    return cudaGetLastError();
+  }
+  k_ray_first<FAST, COUNT><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check, d);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the saved walks are a small share of the rays: 8 blocks per SM at most
+  const int64_t grid2 = std::min<int64_t>(grid, (int64_t)sms * 8);
+  k_ray_resume<FAST, COUNT><<<(unsigned)grid2, kRayBlock, 0, s>>>(a, check, d);
   return cudaGetLastError();
 }
 
 template <bool FAST, bool PAIRS>
-cudaError_t launch_r2(const TraceArgs& a, uint32_t flags, cudaStream_t s) {
+cudaError_t launch_r2(const TraceArgs& a, uint32_t flags, const RayDefer& d, int sms, cudaStream_t s) {
   const int chk = (flags & FX_CHECK_INDEX) ? 1 : 0;
-  return (flags & FX_COUNT) ? launch_r<FAST, PAIRS, true>(a, chk, s) : launch_r<FAST, PAIRS, false>(a, chk, s);
+  return (flags & FX_COUNT) ? launch_r<FAST, PAIRS, true>(a, chk, d, sms, s)
+                            : launch_r<FAST, PAIRS, false>(a, chk, d, sms, s);
 }
 
 }  // namespace
 
-cudaError_t launch_ray(const TraceArgs& a, bool pairs, uint32_t flags, cudaStream_t s) {
+size_t ray_walk_bytes() { return sizeof(RayWalk); }
+
+cudaError_t launch_ray(const TraceArgs& a, bool pairs, uint32_t flags, const RayDefer& d, int sm_count,
+                       cudaStream_t s) {
   if (a.n_ray == 0) return cudaSuccess;
   const bool fast = flags & FX_FAST_MATH;
-  if (pairs) return fast ? launch_r2<true, true>(a, flags, s) : launch_r2<false, true>(a, flags, s);
-  return fast ? launch_r2<true, false>(a, flags, s) : launch_r2<false, false>(a, flags, s);
+  if (pairs)
+    return fast ? launch_r2<true, true>(a, flags, d, sm_count, s) : launch_r2<false, true>(a, flags, d, sm_count, s);
+  return fast ? launch_r2<true, false>(a, flags, d, sm_count, s) : launch_r2<false, false>(a, flags, d, sm_count, s);
 }
 
 }  // namespace fx
