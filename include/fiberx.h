@@ -82,8 +82,8 @@ typedef struct {
 
 /* Persistent kernel variants (fx_launch.variant). */
 #define FX_VARIANT_AUTO 0   /* the library's choice: RAY for rows of at most two candidates on
-                               average (n_pair <= 2 n_ray) on handles of single level-0 pieces,
-                               LANE otherwise */
+                               average (n_pair <= 2 n_ray) on handles without pre-split
+                               segments, LANE otherwise */
 #define FX_VARIANT_LANE 1   /* each lane owns a ray and walks its candidates front to back */
 #define FX_VARIANT_WARP 2   /* a warp owns a ray; its candidates are staged in shared memory */
 #define FX_VARIANT_FILTER 3 /* two phases: the root test of every pair, one lane per pair, then
@@ -102,8 +102,7 @@ typedef struct {
                                (many rays against one fiber).  Closest hits take two passes: rays
                                needing more than 4 node tests save their walk (128 bytes, pool
                                memory for one per ray) and a second pass continues it.  Same
-                               results as LANE.  Handles whose segments are single level-0 pieces
-                               only; elsewhere LANE runs. */
+                               results as LANE, pre-split segments included. */
 
 /* Launch configuration of the persistent kernels (fx_set_launch). */
 typedef struct {

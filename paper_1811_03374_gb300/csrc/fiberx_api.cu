@@ -90,16 +90,16 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
   }
   FX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s));
   int variant = f->launch.variant;
-  // rows of one or two candidates on average: the per-ray kernel without a
-  // queue measured up to 2.6x the lane kernel on such rows (single fibers,
-  // one ray per segment) and at worst 7 % behind it; longer rows: the lane
-  // kernel
+  // rows of one or two candidates on average, segments not pre-split: the
+  // per-ray kernel without a queue measured up to 2.6x the lane kernel on
+  // such rows (single fibers, one ray per segment) and at worst 7 % behind
+  // it; on pre-split segments (0.7x) and longer rows: the lane kernel
   if (variant == FX_VARIANT_AUTO)
     variant = (a.n_pair <= 2 * a.n_ray && f->identity) ? FX_VARIANT_RAY : FX_VARIANT_LANE;
   // the two-phase path covers closest hits on handles of single level-0 pieces
   if (variant == FX_VARIANT_FILTER && (pairs || !f->identity)) variant = FX_VARIANT_LANE;
-  // the scan and per-ray paths cover handles of single level-0 pieces
-  if ((variant == FX_VARIANT_SCAN || variant == FX_VARIANT_RAY) && !f->identity) variant = FX_VARIANT_LANE;
+  // the scan path covers handles of single level-0 pieces
+  if (variant == FX_VARIANT_SCAN && !f->identity) variant = FX_VARIANT_LANE;
   if (variant == FX_VARIANT_FILTER) {
     int2* pass = nullptr;
     int32_t* ibuf = nullptr;

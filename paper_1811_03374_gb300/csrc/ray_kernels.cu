@@ -10,8 +10,11 @@
 // cylinder is hit, the bit-string traversal of Sec. 3.3 -- so the results are
 // the lane kernel's bit for bit.  There is no work queue and no staging:
 // with one candidate per ray the persistent kernels' machinery costs more
-// than the traversal.  Handles whose segments are single level-0 pieces
-// only; others run the lane kernel.
+// than the traversal.  On handles with pre-split segments (IDENTITY false) a
+// candidate's pieces are traversed in order, each to depth d - level, as the
+// lane kernel does there; each piece first takes the bound test on its own
+// root record (the lane kernel tests every piece's root instead: the bound
+// only drops roots that cannot pass, so the results are the same).
 //
 // Closest hits take two passes.  The first gives each ray a budget of node
 // tests.  A ray done within it (most rays against a single fiber miss at the
@@ -54,7 +57,8 @@ struct alignas(16) RayWalk {
   int32_t ray, j, best_seg;   // ray, current candidate, closest hit's segment
   int32_t best_leaf, iters;
   uint32_t bits, start;
-  uint32_t size, slab_ok, pad0, pad1;
+  uint32_t size, slab_ok;
+  int32_t piece, pad0;        // the piece of the candidate (pre-split segments)
 };
 static_assert(sizeof(RayWalk) == 128, "two cache sectors per saved walk");
 
@@ -72,7 +76,7 @@ __device__ __forceinline__ void rotate_piece(const float4* __restrict__ piece, i
 // more than kBudget node tests: `w` then holds its walk, nothing is written,
 // and the events so far are counted.  kWalkResume continues the walk in `w`.
 // Otherwise the ray's result is written and it returns false.
-template <bool FAST, bool PAIRS, bool COUNT, int MODE>
+template <bool FAST, bool PAIRS, bool COUNT, bool IDENTITY, int MODE>
 __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk& w, int check,
                                          uint32_t (&cnt)[5]) {
   static_assert(MODE == kWalkAll || !PAIRS, "the two passes serve closest hits");
@@ -104,55 +108,64 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
     j = w.j;
     resume = true;
   }
-  const int min_size = 1 << piece_min_size_shift(a.depth, 0);
   int used = 0;  // node tests of this pass (kWalkFirst's budget)
   for (; j < cend; ++j) {
     const int32_t s = __ldg(a.seg_idx + j);
     float cand_t = ray_tmax, cand_u = -1.0f;
     int32_t cand_leaf = -1;
-    const float lim = PAIRS ? ray_tmax : best_t;
-    Node R, c;
-    float tmin = 0.0f, tmax = lim, root_r = 0.0f;
-    uint32_t bits = 0, start = 0, size = kRootSize;
-    bool slab_ok = false;
-    int iters = 0;
-    bool test;
-    if (MODE == kWalkResume && resume) {
-      // the saved walk of this candidate; its root is rebuilt by the same
-      // arithmetic as when the first pass began it
-      resume = false;
-      rotate_piece(a.piece, s, rf, R);
-      c = w.c;
-      tmin = w.tmin;
-      tmax = w.tmax;
-      root_r = w.root_r;
-      bits = w.bits;
-      start = w.start;
-      size = w.size;
-      slab_ok = w.slab_ok != 0u;
-      iters = w.iters;
-      test = true;
-    } else {
-      test = s >= 0 && (!check || s < a.n_seg);
-      if (!test) atomicOr(a.status, FX_DEV_BAD_INDEX);
-      if (test) {
-        // bound test on the root record: the sphere that holds the root
-        // node's capped cylinder lies beyond t_max
-        const float4 P = __ldg(a.piece_root + 2 * (int64_t)s), D = __ldg(a.piece_root + 2 * (int64_t)s + 1);
+    const bool resumed = MODE == kWalkResume && resume;
+    if (!resumed && !(s >= 0 && (!check || s < a.n_seg))) {
+      atomicOr(a.status, FX_DEV_BAD_INDEX);
+      if (PAIRS) {
+        a.tu[j] = make_float2(kInf, -1.0f);
+        if (a.leaf) a.leaf[j] = -1;
+      }
+      continue;
+    }
+    // the candidate's pieces: the segment itself, or its pre-split pieces
+    int32_t k = IDENTITY ? s : __ldg(a.piece_begin + s);
+    const int32_t kend = IDENTITY ? s + 1 : __ldg(a.piece_begin + s + 1);
+    if (resumed) k = w.piece;
+    for (; k < kend; ++k) {
+      const int32_t info = IDENTITY ? 0 : __ldg(a.piece_info + k);
+      const uint32_t min_size = 1u << piece_min_size_shift(a.depth, info & 15);
+      Node R, c;
+      float tmin = 0.0f, tmax = PAIRS ? cand_t : best_t, root_r = 0.0f;
+      uint32_t bits = 0, start = 0, size = kRootSize;
+      bool slab_ok = false;
+      int iters = 0;
+      bool test = true;
+      if (MODE == kWalkResume && resume) {
+        // the saved walk of this piece; its root is rebuilt by the same
+        // arithmetic as when the first pass began it
+        resume = false;
+        rotate_piece(a.piece, k, rf, R);
+        c = w.c;
+        tmin = w.tmin;
+        tmax = w.tmax;
+        root_r = w.root_r;
+        bits = w.bits;
+        start = w.start;
+        size = w.size;
+        slab_ok = w.slab_ok != 0u;
+        iters = w.iters;
+      } else {
+        // bound test on the piece's root record: the sphere that holds the
+        // root node's capped cylinder lies beyond t_max
+        const float4 P = __ldg(a.piece_root + 2 * (int64_t)k), D = __ldg(a.piece_root + 2 * (int64_t)k + 1);
         const float px = P.x - rf.o.x, py = P.y - rf.o.y, pz = P.z - rf.o.z;
         const float zp = fmaf(px, rf.w.x, fmaf(py, rf.w.y, pz * rf.w.z));
         const float zd = fmaf(D.x, rf.w.x, fmaf(D.y, rf.w.y, D.z * rf.w.z));
         const float near = fmaf(0.5f, zd, zp) - D.w;
         if (COUNT) ++n_tests;
-        if (near - kBoundSlack * (fabsf(zp) + fabsf(zd) + D.w) > lim) test = false;
+        if (near - kBoundSlack * (fabsf(zp) + fabsf(zd) + D.w) > tmax) test = false;
         root_r = P.w;
+        if (test) {
+          rotate_piece(a.piece, k, rf, R);
+          c = R;
+        }
       }
-      if (test) {
-        rotate_piece(a.piece, s, rf, R);
-        c = R;
-      }
-    }
-    if (test) {
+      if (!test) continue;
       for (;;) {
         if (MODE == kWalkFirst) {
           if (used == kBudget) {  // save the walk for the second pass
@@ -171,6 +184,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
             w.start = start;
             w.size = size;
             w.slab_ok = slab_ok ? 1u : 0u;
+            w.piece = k;
             flush();
             return true;
           }
@@ -188,12 +202,13 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
         over = over && fmaxf(c0, tmin) <= fminf(c1, tmax);
         ++iters;
         if (COUNT) ++n_nodes;
-        if (over && size <= (uint32_t)min_size) {
+        if (over && size <= min_size) {
           const float t = fmaxf(c0, tmin);
           if (t < pair_tmax) {
             float u;
             int32_t lf;
-            to_segment(0, leaf_u<FAST>(c, t, start, size), start, u, lf);
+            to_segment(info, leaf_u<FAST>(c, t, start, size), start, u, lf);
+            if (!IDENTITY && info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
             if (PAIRS) {
               cand_t = t;
               cand_u = u;
@@ -266,24 +281,24 @@ __device__ __forceinline__ void load_walk(const RayWalk* src, RayWalk& w) {
 
 // One thread per ray, the whole walk (per-pair results, or closest hits in
 // one pass).
-template <bool FAST, bool PAIRS, bool COUNT>
+template <bool FAST, bool PAIRS, bool COUNT, bool IDENTITY>
 __global__ void __launch_bounds__(kRayBlock) k_ray(const TraceArgs a, int check) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t cnt[5] = {0, 0, 0, 0, 0};
   RayWalk w;
-  if (r < a.n_ray) ray_walk<FAST, PAIRS, COUNT, kWalkAll>(a, r, w, check, cnt);
+  if (r < a.n_ray) ray_walk<FAST, PAIRS, COUNT, IDENTITY, kWalkAll>(a, r, w, check, cnt);
   add_counts<COUNT>(a, cnt);
 }
 
 // First pass of closest hits.  A ray that runs out of budget takes a slot of
 // the list (one atomic per warp; the list has a slot for every ray).
-template <bool FAST, bool COUNT>
+template <bool FAST, bool COUNT, bool IDENTITY>
 __global__ void __launch_bounds__(kRayBlock) k_ray_first(const TraceArgs a, int check, RayDefer d) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t cnt[5] = {0, 0, 0, 0, 0};
   RayWalk w;
   bool defer = false;
-  if (r < a.n_ray) defer = ray_walk<FAST, false, COUNT, kWalkFirst>(a, r, w, check, cnt);
+  if (r < a.n_ray) defer = ray_walk<FAST, false, COUNT, IDENTITY, kWalkFirst>(a, r, w, check, cnt);
   const unsigned m = __ballot_sync(kFull, defer);
   if (m) {
     const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
@@ -297,7 +312,7 @@ __global__ void __launch_bounds__(kRayBlock) k_ray_first(const TraceArgs a, int 
 }
 
 // Second pass: the saved walks, one thread each, grid-stride over the list.
-template <bool FAST, bool COUNT>
+template <bool FAST, bool COUNT, bool IDENTITY>
 __global__ void __launch_bounds__(kRayBlock) k_ray_resume(const TraceArgs a, int check, RayDefer d) {
   const uint32_t n = min(*d.count, d.capacity);
   uint32_t cnt[5] = {0, 0, 0, 0, 0};
@@ -309,33 +324,39 @@ __global__ void __launch_bounds__(kRayBlock) k_ray_resume(const TraceArgs a, int
     if (i < n) {
       RayWalk w;
       load_walk(reinterpret_cast<const RayWalk*>(d.walks) + i, w);
-      ray_walk<FAST, false, COUNT, kWalkResume>(a, w.ray, w, check, cnt);
+      ray_walk<FAST, false, COUNT, IDENTITY, kWalkResume>(a, w.ray, w, check, cnt);
     }
   }
   add_counts<COUNT>(a, cnt);
 }
 
-template <bool FAST, bool PAIRS, bool COUNT>
+template <bool FAST, bool PAIRS, bool COUNT, bool IDENTITY>
 cudaError_t launch_r(const TraceArgs& a, int check, const RayDefer& d, int sms, cudaStream_t s) {
   const int64_t grid = (a.n_ray + kRayBlock - 1) / kRayBlock;
   if (PAIRS || !d.walks) {
-    k_ray<FAST, PAIRS, COUNT><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check);
+    k_ray<FAST, PAIRS, COUNT, IDENTITY><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check);
     return cudaGetLastError();
   }
-  k_ray_first<FAST, COUNT><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check, d);
+  k_ray_first<FAST, COUNT, IDENTITY><<<(unsigned)grid, kRayBlock, 0, s>>>(a, check, d);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // the saved walks are a small share of the rays: 8 blocks per SM at most
   const int64_t grid2 = std::min<int64_t>(grid, (int64_t)sms * 8);
-  k_ray_resume<FAST, COUNT><<<(unsigned)grid2, kRayBlock, 0, s>>>(a, check, d);
+  k_ray_resume<FAST, COUNT, IDENTITY><<<(unsigned)grid2, kRayBlock, 0, s>>>(a, check, d);
   return cudaGetLastError();
+}
+
+template <bool FAST, bool PAIRS, bool COUNT>
+cudaError_t launch_r1(const TraceArgs& a, int check, const RayDefer& d, int sms, cudaStream_t s) {
+  return a.identity ? launch_r<FAST, PAIRS, COUNT, true>(a, check, d, sms, s)
+                    : launch_r<FAST, PAIRS, COUNT, false>(a, check, d, sms, s);
 }
 
 template <bool FAST, bool PAIRS>
 cudaError_t launch_r2(const TraceArgs& a, uint32_t flags, const RayDefer& d, int sms, cudaStream_t s) {
   const int chk = (flags & FX_CHECK_INDEX) ? 1 : 0;
-  return (flags & FX_COUNT) ? launch_r<FAST, PAIRS, true>(a, chk, d, sms, s)
-                            : launch_r<FAST, PAIRS, false>(a, chk, d, sms, s);
+  return (flags & FX_COUNT) ? launch_r1<FAST, PAIRS, true>(a, chk, d, sms, s)
+                            : launch_r1<FAST, PAIRS, false>(a, chk, d, sms, s);
 }
 
 }  // namespace
