@@ -54,6 +54,7 @@ typedef enum {
 #define FX_DEV_ITER_LIMIT 0x1u  /* a (ray, segment) test hit the per-pair iteration cap */
 #define FX_DEV_UNSUPPORTED 0x2u /* a hit was reported on a piece flagged unsupported */
 #define FX_DEV_BAD_INDEX 0x4u   /* a candidate segment id was out of range (skipped) */
+#define FX_DEV_BAD_DEPTH 0x8u   /* a per-ray depth was outside [0, 23] (clamped to it) */
 
 /* intersect_* flags */
 #define FX_KERNEL_PERSISTENT 0x0u /* default: persistent work-queue kernel */
@@ -174,6 +175,10 @@ fx_status fiber_info(const fx_fibers *f, fx_fibers_info *out);
  * device.
  * depth: subdivision depth d in [0, 23]; leaves have size 2^-d (Sec. 3.3:
  * termination after a fixed number of subdivisions).
+ * ray_depth: nullable; n_ray int8 per-ray depths (device pointer) that
+ * replace `depth` ray by ray, e.g. chosen from each ray's footprint (the
+ * paper's routine takes its termination size per call).  Entries outside
+ * [0, 23] are clamped to it and set FX_DEV_BAD_DEPTH.
  *
  * Candidates are visited in row order, pieces in order; the closest hit so
  * far is the t_max of the next test and only a strictly closer hit replaces
@@ -189,18 +194,20 @@ fx_status fiber_info(const fx_fibers *f, fx_fibers_info *out);
  */
 fx_status intersect_closest(const fx_fibers *f, const float *rays, int64_t n_ray,
                             const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
-                            int32_t depth, uint32_t flags, float *tu, int32_t *seg,
-                            int32_t *leaf, void *stream);
+                            int32_t depth, const int8_t *ray_depth, uint32_t flags, float *tu,
+                            int32_t *seg, int32_t *leaf, void *stream);
 
 /*
  * intersect_pairs -- one result per (ray, candidate) pair, each tested with
  * the ray's own t_max (no pruning across candidates).  Same inputs as
- * intersect_closest; outputs per pair: tu (2 floats) and leaf (nullable).
- * flags: FX_KERNEL_*, FX_FAST_MATH, FX_COUNT, FX_CHECK_INDEX.
+ * intersect_closest (ray_depth included); outputs per pair: tu (2 floats)
+ * and leaf (nullable).  flags: FX_KERNEL_*, FX_FAST_MATH, FX_COUNT,
+ * FX_CHECK_INDEX.
  */
 fx_status intersect_pairs(const fx_fibers *f, const float *rays, int64_t n_ray,
                           const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
-                          int32_t depth, uint32_t flags, float *tu, int32_t *leaf, void *stream);
+                          int32_t depth, const int8_t *ray_depth, uint32_t flags, float *tu,
+                          int32_t *leaf, void *stream);
 
 /*
  * intersect_backward -- adjoint of the closest hit's t with respect to the
@@ -229,7 +236,7 @@ fx_status intersect_backward(const fx_fibers *f, const float *rays, int64_t n_ra
  * routine that computes the intersection's u and normal).
  *
  * Inputs: rays (as above), and tu, seg, leaf from intersect_closest on the
- * same handle at the same depth (leaf is required).  Output: normal, n_ray x
+ * same handle with the same depth and ray_depth (leaf is required).  Output: normal, n_ray x
  * 3 floats, world space, unit length; (0, 0, 0) for misses.  The hit leaf is
  * rebuilt in the ray frame and the hit point projected onto its axis; a
  * lateral hit's normal is the hit point minus that axis point.  A hit on an
@@ -240,8 +247,8 @@ fx_status intersect_backward(const fx_fibers *f, const float *rays, int64_t n_ra
  * Errors: FX_EINVAL (null pointers, negative size), FX_EDEPTH, FX_ECUDA.
  */
 fx_status intersect_normals(const fx_fibers *f, const float *rays, int64_t n_ray, const float *tu,
-                            const int32_t *seg, const int32_t *leaf, int32_t depth, uint32_t flags,
-                            float *normal, void *stream);
+                            const int32_t *seg, const int32_t *leaf, int32_t depth,
+                            const int8_t *ray_depth, uint32_t flags, float *normal, void *stream);
 
 /*
  * intersect_counts -- per-ray pruning-test counts, the statistic of Fig. 8
@@ -269,7 +276,8 @@ fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray,
 /*
  * intersect_closest_host -- intersect_closest on HOST buffers: copies rays,
  * row_ptr and seg_idx to device staging owned by the handle, runs, copies
- * tu / seg / leaf back and synchronises.  Large calls are cut into up to 4
+ * tu / seg / leaf back and synchronises (ray_depth, when given, is a host
+ * array too).  Large calls are cut into up to 4
  * chunks of rows with about equal input bytes; each chunk's copy in, kernels
  * and copy out run on two copy streams owned by the handle and on `stream`,
  * so copies overlap the other chunks' kernels (the naive kernel takes one
@@ -283,8 +291,8 @@ fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray,
  */
 fx_status intersect_closest_host(fx_fibers *f, const float *rays, int64_t n_ray,
                                  const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
-                                 int32_t depth, uint32_t flags, float *tu, int32_t *seg,
-                                 int32_t *leaf, void *stream);
+                                 int32_t depth, const int8_t *ray_depth, uint32_t flags, float *tu,
+                                 int32_t *seg, int32_t *leaf, void *stream);
 
 /*
  * fx_host_bytes -- bytes the last intersect_closest_host call on this handle

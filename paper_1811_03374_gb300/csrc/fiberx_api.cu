@@ -383,13 +383,14 @@ fx_status fx_get_launch(const fx_fibers* f, fx_launch* cfg) {
 }
 
 fx_status intersect_closest(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
-                            const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags, float* tu,
-                            int32_t* seg, int32_t* leaf, void* stream) {
+                            const int32_t* seg_idx, int64_t n_pair, int32_t depth, const int8_t* ray_depth,
+                            uint32_t flags, float* tu, int32_t* seg, int32_t* leaf, void* stream) {
   fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
   if (st != FX_OK) return st;
   if (n_ray > 0 && (!tu || !seg)) return fail(FX_EINVAL, "null tu / seg output");
   cudaStream_t s = (cudaStream_t)stream;
   fx::TraceArgs a = make_args(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  a.ray_depth = ray_depth;
   a.tu = reinterpret_cast<float2*>(tu);
   a.seg = seg;
   a.leaf = leaf;
@@ -408,13 +409,14 @@ fx_status intersect_closest(const fx_fibers* f, const float* rays, int64_t n_ray
 }
 
 fx_status intersect_pairs(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
-                          const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags, float* tu,
-                          int32_t* leaf, void* stream) {
+                          const int32_t* seg_idx, int64_t n_pair, int32_t depth, const int8_t* ray_depth,
+                          uint32_t flags, float* tu, int32_t* leaf, void* stream) {
   fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
   if (st != FX_OK) return st;
   if (n_pair > 0 && !tu) return fail(FX_EINVAL, "null tu output");
   if (flags & FX_POLISH_FP64) return fail(FX_EUNSUPPORTED, "FP64 polish applies to intersect_closest only");
   fx::TraceArgs a = make_args(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
+  a.ray_depth = ray_depth;
   a.tu = reinterpret_cast<float2*>(tu);
   a.leaf = leaf;
   return run_forward(f, a, true, flags, (cudaStream_t)stream);
@@ -446,14 +448,15 @@ fx_status intersect_counts(const fx_fibers* f, const float* rays, int64_t n_ray,
 }
 
 fx_status intersect_normals(const fx_fibers* f, const float* rays, int64_t n_ray, const float* tu,
-                            const int32_t* seg, const int32_t* leaf, int32_t depth, uint32_t flags,
-                            float* normal, void* stream) {
+                            const int32_t* seg, const int32_t* leaf, int32_t depth, const int8_t* ray_depth,
+                            uint32_t flags, float* normal, void* stream) {
   if (!f) return fail(FX_EINVAL, "null fiber handle");
   if (n_ray < 0 || n_ray > 0x7fffffffLL) return fail(FX_EINVAL, "n_ray out of range");
   if (depth < 0 || depth > fx::kMaxDepth) return fail(FX_EDEPTH, "depth outside [0, 23]");
   if (n_ray == 0) return FX_OK;
   if (!rays || !tu || !seg || !leaf || !normal) return fail(FX_EINVAL, "null argument");
   fx::TraceArgs a = make_args(f, rays, n_ray, nullptr, nullptr, 0, depth);
+  a.ray_depth = ray_depth;
   a.tu = reinterpret_cast<float2*>(const_cast<float*>(tu));
   a.seg = const_cast<int32_t*>(seg);
   a.leaf = const_cast<int32_t*>(leaf);
@@ -462,8 +465,8 @@ fx_status intersect_normals(const fx_fibers* f, const float* rays, int64_t n_ray
 }
 
 fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
-                                 const int32_t* seg_idx, int64_t n_pair, int32_t depth, uint32_t flags,
-                                 float* tu, int32_t* seg, int32_t* leaf, void* stream) {
+                                 const int32_t* seg_idx, int64_t n_pair, int32_t depth, const int8_t* ray_depth,
+                                 uint32_t flags, float* tu, int32_t* seg, int32_t* leaf, void* stream) {
   fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
   if (st != FX_OK) return st;
   if (n_ray > 0 && (!tu || !seg)) return fail(FX_EINVAL, "null tu / seg output");
@@ -472,8 +475,8 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t b_rays = al((size_t)n_ray * 32), b_rp = al((size_t)(n_ray + 1) * 4),
                b_si = al((size_t)std::max<int64_t>(n_pair, 1) * 4), b_tu = al((size_t)n_ray * 8),
-               b_seg = al((size_t)n_ray * 4), b_leaf = al((size_t)n_ray * 4);
-  const size_t need = b_rays + b_rp + b_si + b_tu + b_seg + b_leaf;
+               b_seg = al((size_t)n_ray * 4), b_leaf = al((size_t)n_ray * 4), b_dep = al((size_t)n_ray);
+  const size_t need = b_rays + b_rp + b_si + b_tu + b_seg + b_leaf + b_dep;
   if (need > f->stage_bytes) {
     FX_CUDA(cudaStreamSynchronize(s));
     cudaFree(f->stage);
@@ -495,6 +498,7 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   int32_t* d_seg = (int32_t*)(base + b_rays + b_rp + b_si + b_tu);
   int32_t* d_leaf = (leaf || (flags & FX_POLISH_FP64)) ? (int32_t*)(base + b_rays + b_rp + b_si + b_tu + b_seg)
                                                        : nullptr;
+  int8_t* d_dep = ray_depth ? (int8_t*)(base + b_rays + b_rp + b_si + b_tu + b_seg + b_leaf) : nullptr;
 
   // Rows are cut into up to kFxHostChunks chunks of about equal input bytes
   // (32 per ray, 4 per row_ptr entry, 4 per pair), found by bisection on the
@@ -557,6 +561,10 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
       b = run_end;
     }
     f->host_h2d += (n + 1) * 4 + (p1 - p_done) * 4;
+    if (e == cudaSuccess && d_dep && n > 0) {
+      e = cudaMemcpyAsync(d_dep + r0, ray_depth + r0, (size_t)n, cudaMemcpyHostToDevice, f->copy_in);
+      f->host_h2d += n;
+    }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_rp + r0, row_ptr + r0, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, f->copy_in);
     if (e == cudaSuccess && p1 > p_done)
@@ -566,8 +574,8 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
     if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], f->copy_in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[c], 0);
     if (e != cudaSuccess || n == 0) continue;
-    st = intersect_closest(f, d_rays + 8 * r0, n, d_rp + r0, d_si, n_pair, depth, flags, d_tu + 2 * r0, d_seg + r0,
-                           d_leaf ? d_leaf + r0 : nullptr, stream);
+    st = intersect_closest(f, d_rays + 8 * r0, n, d_rp + r0, d_si, n_pair, depth, d_dep ? d_dep + r0 : nullptr,
+                           flags, d_tu + 2 * r0, d_seg + r0, d_leaf ? d_leaf + r0 : nullptr, stream);
     if (st != FX_OK) break;
     e = cudaEventRecord(ev_done[c], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_out, ev_done[c], 0);

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kActiveBlock, 6) k_active(const TraceArgs a, c
   Node c;
   float tmin = 0.0f, tmax = 0.0f, root_r = 0.0f;
   uint32_t bits = 0, start = 0, size = 0;
-  const uint32_t min_size = 1u << piece_min_size_shift(a.depth, 0);
+  uint32_t min_size = 1u << piece_min_size_shift(a.depth, 0);
   int32_t piece = -1, iters = 0;
   bool slab_ok = false;
   uint32_t n_nodes = 0, n_desc = 0, n_back = 0, n_hits = 0;
@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(kActiveBlock, 6) k_active(const TraceArgs a, c
         ray = __ldg(o.active + pool_next + rank);
         float rt = 0.0f;
         rf = load_ray<FAST>(a.rays, ray, rt);
+        min_size = 1u << piece_min_size_shift(depth_of(a, ray), 0);
         best_t = rt;
         best_u = -1.0f;
         best_seg = -1;
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(kActiveBlock, 6) k_active(const TraceArgs a, c
         slab_ok = false;
         if (COUNT) ++n_back;
       }
-      if (!piece_done && iters >= iter_cap(a.depth)) {
+      if (!piece_done && iters >= iter_cap_of(a)) {
         atomicOr(a.status, FX_DEV_ITER_LIMIT);
         piece_done = true;
       }

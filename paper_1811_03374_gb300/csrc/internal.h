@@ -63,7 +63,8 @@ struct TraceArgs {
   int64_t n_ray;
   int64_t n_pair;
   int32_t n_seg;
-  int32_t depth;
+  int32_t depth;             // uniform subdivision depth
+  const int8_t *ray_depth;   // nullable: each ray's own depth
   int32_t chunk;
   int32_t identity;
   float2 *tu;       // per ray (closest) or per pair (pairs)
@@ -74,6 +75,28 @@ struct TraceArgs {
   unsigned long long *counters;  // 5: nodes, descents, backtracks, tests, hits
   unsigned long long *scratch;   // naive kernel: per-ray packed (t, pair) keys
 };
+
+#ifdef __CUDACC__
+// Subdivision depth of ray r: the call's uniform depth, or the ray's own
+// entry of ray_depth, clamped to [0, 23] (FX_DEV_BAD_DEPTH when it was not).
+__device__ __forceinline__ int depth_of(const TraceArgs &a, int64_t r) {
+  if (!a.ray_depth) return a.depth;
+  int d = __ldg(a.ray_depth + r);
+  if (d < 0 || d > kMaxDepth) {
+    atomicOr(a.status, FX_DEV_BAD_DEPTH);
+    d = d < 0 ? 0 : kMaxDepth;
+  }
+  return d;
+}
+// Iteration cap of one (ray, piece) test at a depth: a guard against runaway
+// loops, far above any depth's node count.
+__device__ __forceinline__ int iter_cap(int depth) { return 1024 + 64 * depth; }
+// The cap of a call: its depth's, or with per-ray depths that of depth 23,
+// so that no register holds a ray's depth for it.
+__device__ __forceinline__ int iter_cap_of(const TraceArgs &a) {
+  return iter_cap(a.ray_depth ? kMaxDepth : a.depth);
+}
+#endif
 
 // Work lists of the two-phase path (filter_kernels.cu), allocated per call.
 struct FilterArgs {

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
     st.start = 0;
     st.size = kRootSize;
     st.info = info;
-    st.min_size = 1u << piece_min_size_shift(a.depth, info & 15);
+    st.min_size = 1u << piece_min_size_shift(depth_of(a, ray), info & 15);
     st.iters = 0;
     st.tmax = PAIRS ? cand_t : best_t;
     st.slab_ok = false;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
         st.slab_ok = false;
         if (COUNT) ++n_back;
       }
-      if (!piece_done && st.iters >= iter_cap(a.depth)) {
+      if (!piece_done && st.iters >= iter_cap_of(a)) {
         atomicOr(a.status, FX_DEV_ITER_LIMIT);
         piece_done = true;
       }

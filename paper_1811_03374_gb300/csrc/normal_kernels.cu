@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kNormalBlock) k_normals(const TraceArgs a, con
       }
     }
     const uint32_t start = (uint32_t)(leaf - (off << (23 - lvl))) << lvl;
-    const uint32_t size = 1u << piece_min_size_shift(a.depth, lvl);
+    const uint32_t size = 1u << piece_min_size_shift(depth_of(a, r), lvl);
     const uint32_t seg_size = size >> lvl;  // the leaf's size in segment units
     float tmax_unused;
     const RayFrame rf = load_ray<FAST>(a.rays, r, tmax_unused);

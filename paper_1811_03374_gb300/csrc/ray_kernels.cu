@@ -98,6 +98,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
     rf = load_ray<FAST>(a.rays, r, ray_tmax);
     best_t = ray_tmax;
   }
+  const int rdepth = depth_of(a, r);
   int32_t j = crow;
   bool resume = false;
   if (MODE == kWalkResume) {
@@ -128,7 +129,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
     if (resumed) k = w.piece;
     for (; k < kend; ++k) {
       const int32_t info = IDENTITY ? 0 : __ldg(a.piece_info + k);
-      const uint32_t min_size = 1u << piece_min_size_shift(a.depth, info & 15);
+      const uint32_t min_size = 1u << piece_min_size_shift(rdepth, info & 15);
       Node R, c;
       float tmin = 0.0f, tmax = PAIRS ? cand_t : best_t, root_r = 0.0f;
       uint32_t bits = 0, start = 0, size = kRootSize;
@@ -234,7 +235,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
           slab_ok = false;
           if (COUNT) ++n_back;
         }
-        if (iters >= iter_cap(a.depth)) {
+        if (iters >= iter_cap(rdepth)) {
           atomicOr(a.status, FX_DEV_ITER_LIMIT);
           break;
         }

@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
         ray = e.x;
         cend = e.z;
         const RayFrame rf = load_ray<FAST>(a.rays, ray, ray_tmax);
+        min_size = 1u << piece_min_size_shift(depth_of(a, ray), 0);
         s_fr[0][tid] = make_float4(rf.o.x, rf.o.y, rf.o.z, ray_tmax);
         s_fr[1][tid] = make_float4(rf.w.x, rf.w.y, rf.w.z, PAIRS ? ray_tmax : __int_as_float(-1));
         s_fr[2][tid] = make_float4(rf.e1.x, rf.e1.y, rf.e1.z, -1.0f);
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
         slab_ok = false;
         if (COUNT) ++n_back;
       }
-      if (!piece_done && iters >= iter_cap(a.depth)) {
+      if (!piece_done && iters >= iter_cap_of(a)) {
         atomicOr(a.status, FX_DEV_ITER_LIMIT);
         piece_done = true;
       }

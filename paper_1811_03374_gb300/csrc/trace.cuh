@@ -278,7 +278,6 @@ __device__ __forceinline__ float leaf_u(const Node& c, float t, uint32_t start, 
 // per-(ray, piece) traversal state shared by the kernels
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int iter_cap(int depth) { return 1024 + 64 * depth; }
 
 __device__ __forceinline__ int piece_min_size_shift(int depth, int level) {
   const int d = depth > level ? depth - level : 0;

@@ -21,11 +21,11 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Full traversal of one piece (Sec. 3 / App. C iterative routine).
 template <bool FAST>
-__device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const RayFrame& rf,
+__device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const RayFrame& rf, int depth,
                                             float pair_tmax, float& t_out, float& u_out,
                                             int32_t& leaf_out, unsigned long long* cnt) {
   PairState st;
-  begin_piece<FAST>(st, a.piece, piece, rf, a.identity ? 0 : __ldg(a.piece_info + piece), a.depth, pair_tmax);
+  begin_piece<FAST>(st, a.piece, piece, rf, a.identity ? 0 : __ldg(a.piece_info + piece), depth, pair_tmax);
   for (;;) {
     const float r = cons_radius<FAST>(st.c);
     float c0 = 0.0f, c1 = 0.0f;
@@ -52,7 +52,7 @@ __device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const
       slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
       if (cnt) ++cnt[2];
     }
-    if (st.iters >= iter_cap(a.depth)) {
+    if (st.iters >= iter_cap(depth)) {
       atomicOr(a.status, FX_DEV_ITER_LIMIT);
       return false;
     }
@@ -73,7 +73,7 @@ __device__ __forceinline__ int64_t ray_of_pair(const int32_t* __restrict__ row_p
 
 // Closest over the pieces of one candidate, tested with t_max.
 template <bool FAST>
-__device__ __forceinline__ bool trace_candidate(const TraceArgs& a, int32_t s, const RayFrame& rf,
+__device__ __forceinline__ bool trace_candidate(const TraceArgs& a, int32_t s, const RayFrame& rf, int depth,
                                                 float tmax, float& t, float& u, int32_t& leaf,
                                                 unsigned long long* cnt) {
   int pb = s, pe = s + 1;
@@ -87,7 +87,7 @@ __device__ __forceinline__ bool trace_candidate(const TraceArgs& a, int32_t s, c
     float tk, uk;
     int32_t lk;
     if (cnt) ++cnt[3];
-    if (trace_piece<FAST>(a, k, rf, lim, tk, uk, lk, cnt)) {
+    if (trace_piece<FAST>(a, k, rf, depth, lim, tk, uk, lk, cnt)) {
       lim = tk;
       t = tk;
       u = uk;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_naive(const TraceArgs a) {
     if (CHECK && (s < 0 || s >= a.n_seg)) {
       atomicOr(a.status, FX_DEV_BAD_INDEX);
     } else {
-      got = trace_candidate<FAST>(a, s, rf, ray_tmax, t, u, leaf, COUNT ? cnt : nullptr);
+      got = trace_candidate<FAST>(a, s, rf, depth_of(a, r), ray_tmax, t, u, leaf, COUNT ? cnt : nullptr);
     }
     if (COUNT && got) cnt[4] = 1;
     if (PAIRS) {
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_naive_resolve(const TraceArgs a) {
   const int32_t s = __ldg(a.seg_idx + j);
   float t = kInf, u = -1.0f;
   int32_t leaf = -1;
-  trace_candidate<FAST>(a, s, rf, ray_tmax, t, u, leaf, nullptr);
+  trace_candidate<FAST>(a, s, rf, depth_of(a, r), ray_tmax, t, u, leaf, nullptr);
   a.tu[r] = make_float2(__uint_as_float((uint32_t)(key >> 32)), u);
   a.seg[r] = s;
   if (a.leaf) a.leaf[r] = leaf;
@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(256) k_polish(const TraceArgs a, const float4*
       }
     }
   }
-  const int dl = a.depth > lvl ? a.depth : lvl;
+  const int rd = depth_of(a, r);
+  const int dl = rd > lvl ? rd : lvl;
   const int64_t isize = (int64_t)1 << (23 - dl);
   const double size = (double)isize * (1.0 / 8388608.0);
   // ray frame in FP64 (Duff et al.; any orthonormal frame gives the same result)

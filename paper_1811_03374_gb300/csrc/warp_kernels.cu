@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const int32_t cend = __shfl_sync(kFull, rp1, rr) - s0;
       float ray_tmax;
       const RayFrame rf = load_ray<FAST>(a.rays, ray, ray_tmax);
+      const int rdepth = depth_of(a, ray);  // warp-uniform: one ray per warp
       float best_t = ray_tmax, best_u = -1.0f;
       int32_t best_pos = INT_MAX, best_seg = -1, best_leaf = -1;
       bool active = false;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             cand_u = -1.0f;
             cand_leaf = -1;
             begin_local<FAST>(st, ring[slot][0], ring[slot][1], ring[slot][2], ring[slot][3], rf, info,
-                              a.depth, PAIRS ? ray_tmax : best_t);
+                              rdepth, PAIRS ? ray_tmax : best_t);
             active = true;
             if (COUNT) ++n_tests;
           } else if (PAIRS) {
@@ -198,14 +199,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
               if (COUNT) ++n_hits;
             }
           }
-          if (!piece_done && st.iters >= iter_cap(a.depth)) {
+          if (!piece_done && st.iters >= iter_cap(rdepth)) {
             atomicOr(a.status, FX_DEV_ITER_LIMIT);
             piece_done = true;
           }
           if (piece_done) {
             if (pc < pend) {
               // next piece of a pre-split segment
-              begin_piece<FAST>(st, a.piece, pc, rf, __ldg(a.piece_info + pc), a.depth,
+              begin_piece<FAST>(st, a.piece, pc, rf, __ldg(a.piece_info + pc), rdepth,
                                 PAIRS ? cand_t : best_t);
               ++pc;
               if (COUNT) ++n_tests;

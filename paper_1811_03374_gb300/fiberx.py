@@ -22,6 +22,7 @@ FX_ERRORS = {-1: "FX_EINVAL", -2: "FX_ECUDA", -3: "FX_ENOMEM", -4: "FX_EUNSUPPOR
 FX_DEV_ITER_LIMIT = 0x1
 FX_DEV_UNSUPPORTED = 0x2
 FX_DEV_BAD_INDEX = 0x4
+FX_DEV_BAD_DEPTH = 0x8
 
 FX_KERNEL_PERSISTENT = 0x0
 FX_KERNEL_NAIVE = 0x1
@@ -96,17 +97,17 @@ def lib():
             L.fiber_free.restype = None
             L.fiber_info.argtypes = [vp, ctypes.POINTER(FibersInfo)]
             L.fiber_info.restype = i32
-            L.intersect_closest.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
+            L.intersect_closest.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, u32, vp, vp, vp, vp]
             L.intersect_closest.restype = i32
-            L.intersect_pairs.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp]
+            L.intersect_pairs.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, u32, vp, vp, vp]
             L.intersect_pairs.restype = i32
             L.intersect_backward.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
             L.intersect_backward.restype = i32
             L.intersect_counts.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp]
             L.intersect_counts.restype = i32
-            L.intersect_normals.argtypes = [vp, vp, i64, vp, vp, vp, i32, u32, vp, vp]
+            L.intersect_normals.argtypes = [vp, vp, i64, vp, vp, vp, i32, vp, u32, vp, vp]
             L.intersect_normals.restype = i32
-            L.intersect_closest_host.argtypes = [vp, vp, i64, vp, vp, i64, i32, u32, vp, vp, vp, vp]
+            L.intersect_closest_host.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, u32, vp, vp, vp, vp]
             L.intersect_closest_host.restype = i32
             L.fx_host_bytes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
             L.fx_host_bytes.restype = i32
@@ -243,12 +244,25 @@ def fma_peak(blocks_per_sm=4, iters=4096, stream=None):
     return tf.value, ms.value
 
 
+def _ray_depth(fibers, ray_depth, n_ray):
+    """Per-ray depths as a device int8 tensor of n_ray entries, or None."""
+    import torch
+    if ray_depth is None:
+        return None
+    d = _dev(ray_depth, torch.int8, fibers.device)
+    if d.numel() != n_ray:
+        raise ValueError("ray_depth must have n_ray entries")
+    return d
+
+
 def intersect_closest(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, stream=None,
-                      out=None):
+                      out=None, ray_depth=None):
     """Closest hit per ray: returns (tu [n_ray, 2] f32, seg [n_ray] i32,
-    leaf [n_ray] i32 or None)."""
+    leaf [n_ray] i32 or None).  ray_depth: optional per-ray depths (int8,
+    n_ray) replacing ``depth`` ray by ray."""
     import torch
     rays, row_ptr, seg_idx = _inputs(fibers, rays, row_ptr, seg_idx)
+    rd = _ray_depth(fibers, ray_depth, rays.shape[0])
     n_ray, n_pair = rays.shape[0], seg_idx.numel()
     if out is None:
         tu = torch.empty((n_ray, 2), dtype=torch.float32, device=fibers.device)
@@ -257,7 +271,8 @@ def intersect_closest(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True,
     else:
         tu, seg, lf = out
     _check(lib().intersect_closest(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx), n_pair,
-                                   int(depth), int(flags), _ptr(tu), _ptr(seg), _ptr(lf), _stream(stream)))
+                                   int(depth), _ptr(rd), int(flags), _ptr(tu), _ptr(seg), _ptr(lf),
+                                   _stream(stream)))
     return tu, seg, lf
 
 
@@ -283,15 +298,16 @@ def intersect_closest_noalloc(fibers, rays, row_ptr, seg_idx, depth, flags=0, ou
     return tu, seg, lf
 
 
-def intersect_pairs(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, stream=None):
+def intersect_pairs(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, stream=None, ray_depth=None):
     """Per-pair hits: returns (tu [n_pair, 2], leaf [n_pair] or None)."""
     import torch
     rays, row_ptr, seg_idx = _inputs(fibers, rays, row_ptr, seg_idx)
+    rd = _ray_depth(fibers, ray_depth, rays.shape[0])
     n_ray, n_pair = rays.shape[0], seg_idx.numel()
     tu = torch.empty((n_pair, 2), dtype=torch.float32, device=fibers.device)
     lf = torch.empty(n_pair, dtype=torch.int32, device=fibers.device) if leaf else None
     _check(lib().intersect_pairs(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx), n_pair,
-                                 int(depth), int(flags), _ptr(tu), _ptr(lf), _stream(stream)))
+                                 int(depth), _ptr(rd), int(flags), _ptr(tu), _ptr(lf), _stream(stream)))
     return tu, lf
 
 
@@ -307,18 +323,19 @@ def intersect_counts(fibers, rays, row_ptr, seg_idx, depth, boxes=False, flags=0
     return n.to(torch.int64) & 0xffffffff
 
 
-def intersect_normals(fibers, rays, tu, seg, leaf, depth, flags=0, stream=None, out=None):
+def intersect_normals(fibers, rays, tu, seg, leaf, depth, flags=0, stream=None, out=None, ray_depth=None):
     """Unit surface normals [n_ray, 3] at the closest hits (tu, seg, leaf from
-    intersect_closest at `depth`); zero for misses."""
+    intersect_closest at `depth` and `ray_depth`); zero for misses."""
     import torch
     dev = fibers.device
     rays = _dev(rays, torch.float32, dev)
     tu = _dev(tu, torch.float32, dev)
     seg = _dev(seg, torch.int32, dev)
     leaf = _dev(leaf, torch.int32, dev)
+    rd = _ray_depth(fibers, ray_depth, rays.shape[0])
     n = out if out is not None else torch.empty((rays.shape[0], 3), dtype=torch.float32, device=dev)
     _check(lib().intersect_normals(fibers.handle, _ptr(rays), rays.shape[0], _ptr(tu), _ptr(seg), _ptr(leaf),
-                                   int(depth), int(flags), _ptr(n), _stream(stream)))
+                                   int(depth), _ptr(rd), int(flags), _ptr(n), _stream(stream)))
     return n
 
 
@@ -339,7 +356,8 @@ def intersect_backward(fibers, rays, tu, seg, grad_t, grad_cps=None, stream=None
     return grad_cps, skipped
 
 
-def intersect_closest_host(fibers, rays, row_ptr, seg_idx, depth, flags=0, out=None, stream=None):
+def intersect_closest_host(fibers, rays, row_ptr, seg_idx, depth, flags=0, out=None, stream=None,
+                           ray_depth=None):
     """intersect_closest on host (numpy or CPU torch, ideally pinned) buffers;
     returns host (tu, seg, leaf) and synchronises."""
     import torch
@@ -351,12 +369,15 @@ def intersect_closest_host(fibers, rays, row_ptr, seg_idx, depth, flags=0, out=N
 
     rays, row_ptr, seg_idx = host(rays, torch.float32), host(row_ptr, torch.int32), host(seg_idx, torch.int32)
     n_ray, n_pair = rays.shape[0], seg_idx.numel()
+    rd = host(ray_depth, torch.int8) if ray_depth is not None else None
+    if rd is not None and rd.numel() != n_ray:
+        raise ValueError("ray_depth must have n_ray entries")
     if out is None:
         out = (torch.empty((n_ray, 2), dtype=torch.float32), torch.empty(n_ray, dtype=torch.int32),
                torch.empty(n_ray, dtype=torch.int32))
     tu, seg, lf = out
     _check(lib().intersect_closest_host(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx),
-                                        n_pair, int(depth), int(flags), _ptr(tu), _ptr(seg), _ptr(lf),
+                                        n_pair, int(depth), _ptr(rd), int(flags), _ptr(tu), _ptr(seg), _ptr(lf),
                                         _stream(stream)))
     return tu, seg, lf
 
