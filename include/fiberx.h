@@ -200,14 +200,18 @@ fx_status intersect_closest(const fx_fibers *f, const float *rays, int64_t n_ray
 /*
  * intersect_pairs -- one result per (ray, candidate) pair, each tested with
  * the ray's own t_max (no pruning across candidates).  Same inputs as
- * intersect_closest (ray_depth included); outputs per pair: tu (2 floats)
- * and leaf (nullable).  flags: FX_KERNEL_*, FX_FAST_MATH, FX_COUNT,
- * FX_CHECK_INDEX.
+ * intersect_closest (ray_depth included); outputs per pair: tu (2 floats),
+ * leaf (nullable) and pair_flags (nullable, one byte per pair: the FX_DEV_*
+ * bits -- iteration cap, unsupported piece hit, bad segment id -- that this
+ * pair's test raised, a hit on an unsupported piece counting even when a
+ * later piece of the segment replaced it; the sticky status word gets them
+ * too).  flags:
+ * FX_KERNEL_*, FX_FAST_MATH, FX_COUNT, FX_CHECK_INDEX.
  */
 fx_status intersect_pairs(const fx_fibers *f, const float *rays, int64_t n_ray,
                           const int32_t *row_ptr, const int32_t *seg_idx, int64_t n_pair,
                           int32_t depth, const int8_t *ray_depth, uint32_t flags, float *tu,
-                          int32_t *leaf, void *stream);
+                          int32_t *leaf, uint8_t *pair_flags, void *stream);
 
 /*
  * intersect_backward -- adjoint of the closest hit's t with respect to the

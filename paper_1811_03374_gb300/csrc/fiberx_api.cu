@@ -410,7 +410,7 @@ fx_status intersect_closest(const fx_fibers* f, const float* rays, int64_t n_ray
 
 fx_status intersect_pairs(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
                           const int32_t* seg_idx, int64_t n_pair, int32_t depth, const int8_t* ray_depth,
-                          uint32_t flags, float* tu, int32_t* leaf, void* stream) {
+                          uint32_t flags, float* tu, int32_t* leaf, uint8_t* pair_flags, void* stream) {
   fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
   if (st != FX_OK) return st;
   if (n_pair > 0 && !tu) return fail(FX_EINVAL, "null tu output");
@@ -419,6 +419,7 @@ fx_status intersect_pairs(const fx_fibers* f, const float* rays, int64_t n_ray, 
   a.ray_depth = ray_depth;
   a.tu = reinterpret_cast<float2*>(tu);
   a.leaf = leaf;
+  a.pair_flags = pair_flags;
   return run_forward(f, a, true, flags, (cudaStream_t)stream);
 }
 

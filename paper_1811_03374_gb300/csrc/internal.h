@@ -70,6 +70,7 @@ struct TraceArgs {
   float2 *tu;       // per ray (closest) or per pair (pairs)
   int32_t *seg;     // per ray (closest only)
   int32_t *leaf;    // nullable
+  uint8_t *pair_flags;  // pairs only, nullable: FX_DEV_* bits of each pair's test
   uint32_t *queue;
   uint32_t *status;
   unsigned long long *counters;  // 5: nodes, descents, backtracks, tests, hits

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
   int32_t best_seg = -1, best_leaf = -1;
   float cand_t = 0.0f, cand_u = -1.0f;
   int32_t cand_leaf = -1;
+  uint32_t cand_flags = 0;  // FX_DEV_* bits of the current pair (per-pair mode)
   bool active = false, done = false;
   Lite st;
   uint32_t n_nodes = 0, n_desc = 0, n_back = 0, n_tests = 0, n_hits = 0;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
     if (PAIRS) {
       a.tu[cand] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
       if (a.leaf) a.leaf[cand] = cand_leaf;
+      if (a.pair_flags) a.pair_flags[cand] = (uint8_t)cand_flags;
     }
   };
   // Moves to the next candidate of the ray (or finishes the ray).  A lane
@@ -198,9 +200,11 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
         cand_t = ray_tmax;
         cand_u = -1.0f;
         cand_leaf = -1;
+        cand_flags = 0;
       }
       if (!valid(s_cur)) {
         atomicOr(a.status, FX_DEV_BAD_INDEX);
+        if (PAIRS) cand_flags |= FX_DEV_BAD_INDEX;
         s_cur = -1;
       }
       if (IDENTITY) {
@@ -315,7 +319,10 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
           float u;
           int32_t lf;
           to_segment(st.info, leaf_u<FAST>(st.c, t, st.start, st.size), st.start, u, lf);
-          if (st.info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
+          if (st.info < 0) {
+            atomicOr(a.status, FX_DEV_UNSUPPORTED);
+            if (PAIRS) cand_flags |= FX_DEV_UNSUPPORTED;
+          }
           if (PAIRS) {
             cand_t = t;
             cand_u = u;
@@ -345,6 +352,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
       }
       if (!piece_done && st.iters >= iter_cap_of(a)) {
         atomicOr(a.status, FX_DEV_ITER_LIMIT);
+        if (PAIRS) cand_flags |= FX_DEV_ITER_LIMIT;
         piece_done = true;
       }
       if (piece_done) active = false;

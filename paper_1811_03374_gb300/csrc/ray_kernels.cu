@@ -114,12 +114,14 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
     const int32_t s = __ldg(a.seg_idx + j);
     float cand_t = ray_tmax, cand_u = -1.0f;
     int32_t cand_leaf = -1;
+    uint32_t cand_flags = 0;  // FX_DEV_* bits of this pair (per-pair mode)
     const bool resumed = MODE == kWalkResume && resume;
     if (!resumed && !(s >= 0 && (!check || s < a.n_seg))) {
       atomicOr(a.status, FX_DEV_BAD_INDEX);
       if (PAIRS) {
         a.tu[j] = make_float2(kInf, -1.0f);
         if (a.leaf) a.leaf[j] = -1;
+        if (a.pair_flags) a.pair_flags[j] = FX_DEV_BAD_INDEX;
       }
       continue;
     }
@@ -209,7 +211,10 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
             float u;
             int32_t lf;
             to_segment(info, leaf_u<FAST>(c, t, start, size), start, u, lf);
-            if (!IDENTITY && info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
+            if (!IDENTITY && info < 0) {
+              atomicOr(a.status, FX_DEV_UNSUPPORTED);
+              cand_flags |= FX_DEV_UNSUPPORTED;
+            }
             if (PAIRS) {
               cand_t = t;
               cand_u = u;
@@ -237,6 +242,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
         }
         if (iters >= iter_cap(rdepth)) {
           atomicOr(a.status, FX_DEV_ITER_LIMIT);
+          cand_flags |= FX_DEV_ITER_LIMIT;
           break;
         }
       }
@@ -244,6 +250,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
     if (PAIRS) {
       a.tu[j] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
       if (a.leaf) a.leaf[j] = cand_leaf;
+      if (a.pair_flags) a.pair_flags[j] = (uint8_t)cand_flags;
     }
   }
   if (!PAIRS) {

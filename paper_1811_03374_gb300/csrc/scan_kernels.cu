@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
         if (PAIRS && !pass) {
           a.tu[j] = make_float2(kInf, -1.0f);
           if (a.leaf) a.leaf[j] = -1;
+          if (a.pair_flags) a.pair_flags[j] = valid ? 0 : FX_DEV_BAD_INDEX;
         }
       }
       if (lane == L) {
@@ -455,15 +456,17 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
         slab_ok = false;
         if (COUNT) ++n_back;
       }
+      bool capped = false;
       if (!piece_done && iters >= iter_cap_of(a)) {
         atomicOr(a.status, FX_DEV_ITER_LIMIT);
-        piece_done = true;
+        piece_done = capped = true;
       }
       if (piece_done) {
         active = false;
         if (PAIRS) {
           a.tu[cand_j] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
           if (a.leaf) a.leaf[cand_j] = cand_leaf;
+          if (a.pair_flags) a.pair_flags[cand_j] = capped ? FX_DEV_ITER_LIMIT : 0;
         }
       }
     }

@@ -23,7 +23,7 @@ constexpr unsigned kFull = 0xffffffffu;
 template <bool FAST>
 __device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const RayFrame& rf, int depth,
                                             float pair_tmax, float& t_out, float& u_out,
-                                            int32_t& leaf_out, unsigned long long* cnt) {
+                                            int32_t& leaf_out, unsigned long long* cnt, uint32_t& flags) {
   PairState st;
   begin_piece<FAST>(st, a.piece, piece, rf, a.identity ? 0 : __ldg(a.piece_info + piece), depth, pair_tmax);
   for (;;) {
@@ -38,7 +38,10 @@ __device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const
       if (!(t < pair_tmax)) return false;
       const float up = leaf_u<FAST>(st.c, t, st.start, st.size);
       to_segment(st.info, up, st.start, u_out, leaf_out);
-      if (st.info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
+      if (st.info < 0) {
+        atomicOr(a.status, FX_DEV_UNSUPPORTED);
+        flags |= FX_DEV_UNSUPPORTED;
+      }
       t_out = t;
       return true;
     } else if (over) {
@@ -54,6 +57,7 @@ __device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const
     }
     if (st.iters >= iter_cap(depth)) {
       atomicOr(a.status, FX_DEV_ITER_LIMIT);
+      flags |= FX_DEV_ITER_LIMIT;
       return false;
     }
   }
@@ -75,7 +79,7 @@ __device__ __forceinline__ int64_t ray_of_pair(const int32_t* __restrict__ row_p
 template <bool FAST>
 __device__ __forceinline__ bool trace_candidate(const TraceArgs& a, int32_t s, const RayFrame& rf, int depth,
                                                 float tmax, float& t, float& u, int32_t& leaf,
-                                                unsigned long long* cnt) {
+                                                unsigned long long* cnt, uint32_t& flags) {
   int pb = s, pe = s + 1;
   if (!a.identity) {
     pb = __ldg(a.piece_begin + s);
@@ -87,7 +91,7 @@ __device__ __forceinline__ bool trace_candidate(const TraceArgs& a, int32_t s, c
     float tk, uk;
     int32_t lk;
     if (cnt) ++cnt[3];
-    if (trace_piece<FAST>(a, k, rf, depth, lim, tk, uk, lk, cnt)) {
+    if (trace_piece<FAST>(a, k, rf, depth, lim, tk, uk, lk, cnt, flags)) {
       lim = tk;
       t = tk;
       u = uk;
@@ -110,15 +114,18 @@ __global__ void __launch_bounds__(256) k_naive(const TraceArgs a) {
     float t = kInf, u = -1.0f;
     int32_t leaf = -1;
     bool got = false;
-    if (CHECK && (s < 0 || s >= a.n_seg)) {
+    uint32_t flags = 0;  // FX_DEV_* bits of this pair
+    if (s < 0 || (CHECK && s >= a.n_seg)) {
       atomicOr(a.status, FX_DEV_BAD_INDEX);
+      flags = FX_DEV_BAD_INDEX;
     } else {
-      got = trace_candidate<FAST>(a, s, rf, depth_of(a, r), ray_tmax, t, u, leaf, COUNT ? cnt : nullptr);
+      got = trace_candidate<FAST>(a, s, rf, depth_of(a, r), ray_tmax, t, u, leaf, COUNT ? cnt : nullptr, flags);
     }
     if (COUNT && got) cnt[4] = 1;
     if (PAIRS) {
       a.tu[j] = make_float2(got ? t : kInf, got ? u : -1.0f);
       if (a.leaf) a.leaf[j] = got ? leaf : -1;
+      if (a.pair_flags) a.pair_flags[j] = (uint8_t)flags;
     } else if (got) {
       // t >= 0, so its bit pattern orders like the value; ties keep the
       // smaller pair index (the earlier candidate)
@@ -153,7 +160,8 @@ __global__ void __launch_bounds__(256) k_naive_resolve(const TraceArgs a) {
   const int32_t s = __ldg(a.seg_idx + j);
   float t = kInf, u = -1.0f;
   int32_t leaf = -1;
-  trace_candidate<FAST>(a, s, rf, depth_of(a, r), ray_tmax, t, u, leaf, nullptr);
+  uint32_t flags = 0;
+  trace_candidate<FAST>(a, s, rf, depth_of(a, r), ray_tmax, t, u, leaf, nullptr, flags);
   a.tu[r] = make_float2(__uint_as_float((uint32_t)(key >> 32)), u);
   a.seg[r] = s;
   if (a.leaf) a.leaf[r] = leaf;

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         if (pos < n_stream) {
           const int slot = pos & (kSlots - 1);
           int32_t s = pre;
-          if (CHECK && (s < 0 || s >= a.n_seg)) {
+          if (s < 0 || (CHECK && s >= a.n_seg)) {
             atomicOr(a.status, FX_DEV_BAD_INDEX);
             s = -1;
           }
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       int32_t my_pos = -1, my_seg = -1, pc = 0, pend = 0;
       float cand_t = 0.0f, cand_u = -1.0f;  // pairs mode: best over the candidate's pieces
       int32_t cand_leaf = -1;
+      uint32_t cand_flags = 0;  // FX_DEV_* bits of the lane's pair (pairs mode)
 
       for (;;) {
         // everything but the latest request is complete; publish warp-wide
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             cand_t = ray_tmax;
             cand_u = -1.0f;
             cand_leaf = -1;
+            cand_flags = 0;
             begin_local<FAST>(st, ring[slot][0], ring[slot][1], ring[slot][2], ring[slot][3], rf, info,
                               rdepth, PAIRS ? ray_tmax : best_t);
             active = true;
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           } else if (PAIRS) {
             a.tu[s0 + my_pos] = make_float2(kInf, -1.0f);
             if (a.leaf) a.leaf[s0 + my_pos] = -1;
+            if (a.pair_flags) a.pair_flags[s0 + my_pos] = FX_DEV_BAD_INDEX;
           }
         }
         consumed += take;
@@ -185,7 +188,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
               float u;
               int32_t lf;
               to_segment(st.info, leaf_u<FAST>(st.c, t, st.start, st.size), st.start, u, lf);
-              if (st.info < 0) atomicOr(a.status, FX_DEV_UNSUPPORTED);
+              if (st.info < 0) {
+                atomicOr(a.status, FX_DEV_UNSUPPORTED);
+                cand_flags |= FX_DEV_UNSUPPORTED;
+              }
               if (PAIRS) {
                 cand_t = t;
                 cand_u = u;
@@ -201,6 +207,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           }
           if (!piece_done && st.iters >= iter_cap(rdepth)) {
             atomicOr(a.status, FX_DEV_ITER_LIMIT);
+            cand_flags |= FX_DEV_ITER_LIMIT;
             piece_done = true;
           }
           if (piece_done) {
@@ -215,6 +222,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
               if (PAIRS) {
                 a.tu[s0 + my_pos] = make_float2(cand_t < ray_tmax ? cand_t : kInf, cand_u);
                 if (a.leaf) a.leaf[s0 + my_pos] = cand_leaf;
+                if (a.pair_flags) a.pair_flags[s0 + my_pos] = (uint8_t)cand_flags;
               }
             }
           }

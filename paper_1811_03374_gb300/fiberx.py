@@ -99,7 +99,7 @@ def lib():
             L.fiber_info.restype = i32
             L.intersect_closest.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, u32, vp, vp, vp, vp]
             L.intersect_closest.restype = i32
-            L.intersect_pairs.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, u32, vp, vp, vp]
+            L.intersect_pairs.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, u32, vp, vp, vp, vp]
             L.intersect_pairs.restype = i32
             L.intersect_backward.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
             L.intersect_backward.restype = i32
@@ -298,17 +298,20 @@ def intersect_closest_noalloc(fibers, rays, row_ptr, seg_idx, depth, flags=0, ou
     return tu, seg, lf
 
 
-def intersect_pairs(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, stream=None, ray_depth=None):
-    """Per-pair hits: returns (tu [n_pair, 2], leaf [n_pair] or None)."""
+def intersect_pairs(fibers, rays, row_ptr, seg_idx, depth, flags=0, leaf=True, stream=None, ray_depth=None,
+                    pair_flags=False):
+    """Per-pair hits: returns (tu [n_pair, 2], leaf [n_pair] or None), and
+    with pair_flags=True also the FX_DEV_* bits of each pair [n_pair] uint8."""
     import torch
     rays, row_ptr, seg_idx = _inputs(fibers, rays, row_ptr, seg_idx)
     rd = _ray_depth(fibers, ray_depth, rays.shape[0])
     n_ray, n_pair = rays.shape[0], seg_idx.numel()
     tu = torch.empty((n_pair, 2), dtype=torch.float32, device=fibers.device)
     lf = torch.empty(n_pair, dtype=torch.int32, device=fibers.device) if leaf else None
+    pf = torch.empty(n_pair, dtype=torch.uint8, device=fibers.device) if pair_flags else None
     _check(lib().intersect_pairs(fibers.handle, _ptr(rays), n_ray, _ptr(row_ptr), _ptr(seg_idx), n_pair,
-                                 int(depth), _ptr(rd), int(flags), _ptr(tu), _ptr(lf), _stream(stream)))
-    return tu, lf
+                                 int(depth), _ptr(rd), int(flags), _ptr(tu), _ptr(lf), _ptr(pf), _stream(stream)))
+    return (tu, lf, pf) if pair_flags else (tu, lf)
 
 
 def intersect_counts(fibers, rays, row_ptr, seg_idx, depth, boxes=False, flags=0, stream=None):

@@ -43,7 +43,7 @@ def test_argument_errors_without_device():
     assert L.fiber_upload(None, 0, 0, ctypes.byref(opts), None, ctypes.byref(h)) == -1
     # null handle
     assert L.intersect_closest(None, None, 0, None, None, 0, 8, None, 0, None, None, None, None) == -1
-    assert L.intersect_pairs(None, None, 0, None, None, 0, 8, None, 0, None, None, None) == -1
+    assert L.intersect_pairs(None, None, 0, None, None, 0, 8, None, 0, None, None, None, None) == -1
     assert L.intersect_normals(None, None, 0, None, None, None, 8, None, 0, None, None) == -1
     assert L.intersect_closest_host(None, None, 0, None, None, 0, 8, None, 0, None, None, None, None) == -1
     assert L.intersect_backward(None, None, 0, None, None, None, None, None, None) == -1
