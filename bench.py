@@ -179,8 +179,9 @@ def profiled_traffic(variant):
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_rate(case, depth, seconds, seed=7):
-    """Times the FP64 oracle on a seeded ray sample sized to ~`seconds`."""
+def oracle_rate(case, depth, seconds, seed=7, nthreads=0):
+    """Times the FP64 oracle on a seeded ray sample sized to ~`seconds`
+    (nthreads 0: all host cores)."""
     import oracle as O
     from paper_1811_03374_gb300 import inputs as I
     g = np.random.default_rng(seed)
@@ -191,7 +192,7 @@ def oracle_rate(case, depth, seconds, seed=7):
         idx = np.sort(g.choice(n, max(1, int(frac * n)), replace=False))
         sub = I.subsample_rays(case, idx)
         t0 = time.perf_counter()
-        O.closest(sub, depth, pieces)
+        O.closest(sub, depth, pieces, nthreads=nthreads)
         dt = time.perf_counter() - t0
         pairs = len(sub["seg_idx"])
         if dt >= 0.5 * seconds or frac >= 1.0:
@@ -200,12 +201,12 @@ def oracle_rate(case, depth, seconds, seed=7):
     reps = 1
     while dt * reps < 0.5 * seconds:  # the whole frame is cheap: repeat it
         t0 = time.perf_counter()
-        O.closest(sub, depth, pieces)
+        O.closest(sub, depth, pieces, nthreads=nthreads)
         dt_r = time.perf_counter() - t0
         dt = (dt * reps + dt_r) / (reps + 1)
         reps += 1
     return dict(value=pairs / dt / 1e9, pairs=pairs, rays=len(idx), seconds=dt * reps, frac=len(idx) / n,
-                cores=O.num_threads(), reps=reps)
+                cores=nthreads or O.num_threads(), reps=reps)
 
 
 def run_reference(args):
@@ -405,10 +406,14 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:  # rank 0 at N = 1 only
         r = oracle_rate(case, depth, args.cpu_seconds)
+        r1 = oracle_rate(case, depth, max(2.0, args.cpu_seconds / 4), seed=8, nthreads=1)
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": "%d seeded rays (%.2f%% of the frame) with their %d candidate pairs, "
                          "FP64 oracle, OpenMP over rays, %d repetition(s), %.1f s" % (
-                             r["rays"], 100 * r["frac"], r["pairs"], r["reps"], r["seconds"])}
+                             r["rays"], 100 * r["frac"], r["pairs"], r["reps"], r["seconds"]),
+               "single_core": {"value": r1["value"], "unit": UNIT, "cores": 1,
+                               "sample": "%d seeded rays with their %d candidate pairs, %.1f s" % (
+                                   r1["rays"], r1["pairs"], r1["seconds"])}}
 
     emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
