@@ -32,7 +32,6 @@ sys.path.insert(0, ROOT)
 METRIC = "G ray–segment intersections/s at depth d (FP32 vs oracle tol) and % FP32 FMA peak"
 UNIT = "G intersections/s"
 WORKLOAD = "hair_patch_1080p"
-DEFAULT_DEPTH = 10
 
 
 def parse():
@@ -215,7 +214,10 @@ def run_reference(args):
         return
     import oracle as O
     case = load_workload()
-    depth = args.depth if args.depth is not None else DEFAULT_DEPTH
+    # the depth the GPU arm runs: the tuned one cached for this workload
+    from paper_1811_03374_gb300 import tune as T
+    depth = args.depth if args.depth is not None else T.cached_depth(
+        int(case["cps"].shape[0]), int(case["rays"].shape[0]), len(case["seg_idx"]))
     # size one step to ~ (a few minutes / steps)
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     probe = oracle_rate(case, depth, per_step)

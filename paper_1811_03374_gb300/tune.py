@@ -48,6 +48,17 @@ def _load():
         return {}
 
 
+def cached_depth(n_seg, n_ray, n_pair):
+    """The depth cached for a workload of these sizes (on whichever GPU it
+    was tuned), else the default: what the GPU run takes without retuning,
+    for callers without a GPU to key on."""
+    suffix = "|seg=%d|ray=%d|pair=%d" % (n_seg, n_ray, n_pair)
+    for k, v in _load().items():
+        if k.endswith(suffix):
+            return int(v.get("depth", DEFAULT["depth"]))
+    return DEFAULT["depth"]
+
+
 def select_depth(fib, rays, row_ptr, seg_idx, cps, sample=200_000, tol_r=1e-3, quantile=0.999,
                  flags=0, depths=range(2, 23)):
     """Smallest depth whose hits match depth 22 within tol_r * r(u)."""
