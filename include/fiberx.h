@@ -337,7 +337,8 @@ fx_status fx_stream_status(fx_fibers *f, void *stream, uint32_t *device_flags);
  * ray, on each call.  This entry point allocates nothing: the keys live in a
  * fixed device array of FX_NOALLOC_MAX_RAYS entries (8 MiB) that every GPU
  * loading the library holds until the process exits.  The caller passes the
- * handle, inputs and outputs exactly as for intersect_closest; n_ray above
+ * handle, inputs and outputs as for intersect_closest (uniform depth only, no
+ * ray_depth); n_ray above
  * FX_NOALLOC_MAX_RAYS is refused with FX_EINVAL.  Results equal
  * intersect_closest with FX_KERNEL_NAIVE and the same flags (FX_FAST_MATH,
  * FX_COUNT, FX_CHECK_INDEX; FX_POLISH_FP64 needs a non-null leaf).
