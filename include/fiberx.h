@@ -258,9 +258,10 @@ fx_status intersect_normals(const fx_fibers *f, const float *rays, int64_t n_ray
  * intersect_counts -- per-ray pruning-test counts, the statistic of Fig. 8
  * (oriented bounding cylinders against axis-aligned boxes).
  *
- * Same inputs as intersect_closest.  Each ray's candidates are searched in
- * row order with the closest hit so far as t_max, with no test before the
- * root's, so only the bounding volume differs:
+ * Same inputs as intersect_closest (uniform depth only).  Each ray's
+ * candidates are searched in row order with the closest hit so far as
+ * t_max, with no test before the root's, so only the bounding volume
+ * differs:
  *   - default: the traversal of Sec. 3.3; one count per node tested;
  *   - FX_COUNT_BOXES: the same subdivision without partition planes, each
  *     node bounded by the box [min_k (q_k - r_k), max_k (q_k + r_k)] of its
