@@ -90,8 +90,15 @@ __device__ __forceinline__ int depth_of(const TraceArgs &a, int64_t r) {
   return d;
 }
 // Iteration cap of one (ray, piece) test at a depth: a guard against runaway
-// loops, far above any depth's node count.
-__device__ __forceinline__ int iter_cap(int depth) { return 1024 + 64 * depth; }
+// loops, far above any depth's node count.  (Compile-time settings, so that
+// a test build can make the guard trip.)
+#ifndef FX_ITER_CAP_BASE
+#define FX_ITER_CAP_BASE 1024
+#endif
+#ifndef FX_ITER_CAP_PER_LEVEL
+#define FX_ITER_CAP_PER_LEVEL 64
+#endif
+__device__ __forceinline__ int iter_cap(int depth) { return FX_ITER_CAP_BASE + FX_ITER_CAP_PER_LEVEL * depth; }
 // The cap of a call: its depth's, or with per-ray depths that of depth 23,
 // so that no register holds a ray's depth for it.
 __device__ __forceinline__ int iter_cap_of(const TraceArgs &a) {
