@@ -21,7 +21,7 @@ def test_fig3_curve_is_valid():
 
 
 def test_fig4_loop_is_invalid():
-    # Fig. 4: the loop "violating the constraints" must be rejected.
+    # Fig. 4: the loop, which violates the constraints, must be rejected.
     cp = _load("fig4_loop.txt")
     assert not O.valid_cubic(cp)
     P = cp[:, :3]
