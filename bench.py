@@ -161,9 +161,10 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(variant):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the variant's kernel."""
+def profiled(variant, field="dram_bytes_per_launch"):
+    """A per-launch figure of the committed ncu summary (DRAM bytes, warp
+    instructions), if it was taken on the current source of the variant's
+    kernel."""
     if variant not in TRAFFIC:
         return None
     key, files = TRAFFIC[variant]
@@ -171,7 +172,7 @@ def profiled_traffic(variant):
     try:
         e = json.load(open(path)).get(key)
         if e and e.get("source_hash") == source_hash(files):
-            return e.get("dram_bytes_per_launch")
+            return e.get(field)
     except Exception:
         pass
     return None
@@ -391,7 +392,9 @@ def main():
     peak = FL.fp32_peak_tflops(sm, 2070.0)
     fma_tflops, _ = F.fma_peak()  # measured FP32 FMA throughput, the cross-check of `peak`
     achieved = work / (ms_step * 1e-3) / 1e12
-    traffic = profiled_traffic(fib.get_launch()["variant"]) if args.kernel == "persistent" else None
+    variant = fib.get_launch()["variant"]
+    traffic = profiled(variant) if args.kernel == "persistent" else None
+    winst = profiled(variant, "warp_inst_per_launch") if args.kernel == "persistent" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)" % sm,
@@ -403,6 +406,14 @@ def main():
                 "frac_method_equivalent": mwork / (ms_step * 1e-3) / 1e12 / peak,
                 "hbm_gbs_algorithmic": abytes / (ms_step * 1e-3) / 1e9,
                 "alg_bytes_per_launch": abytes}
+    if winst:
+        # what binds the kernel: instruction issue, one warp instruction per
+        # cycle on each of an SM's 4 schedulers (the ncu count per launch
+        # over the live time)
+        issue_peak = sm * 4 * 2070.0e6 / 1e9
+        issue = winst / (ms_step * 1e-3) / 1e9
+        roofline["issue"] = {"warp_inst_per_launch": winst, "achieved": issue, "peak": issue_peak,
+                             "unit": "G warp instructions/s", "frac": issue / issue_peak}
     if clk:
         roofline["frac_at_sampled_clock"] = achieved / FL.fp32_peak_tflops(sm, clk["sm_mhz"])
 
