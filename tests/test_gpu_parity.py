@@ -564,3 +564,29 @@ def test_hair_patch_full_size_sampled(hair, flags, depth, variant):
     assert stats["hits"] > 500
     # rays with no candidates are misses
     assert np.all(seg[counts == 0] == -1)
+
+
+def test_host_entry_edge_cases():
+    # no rays; rays without any candidate (no pairs at all); a single ray;
+    # per-ray depths from host memory
+    case = I.sweep_case("moderate", 64, forced_hits=True)
+    fib = F.Fibers(case["cps"])
+    empty_rays = np.zeros((0, 8), np.float32)
+    tu, seg, lf = F.intersect_closest_host(fib, empty_rays, np.zeros(1, np.int32), np.zeros(0, np.int32), 8)
+    assert tu.shape[0] == 0 and seg.shape[0] == 0
+    n = len(case["rays"])
+    tu, seg, lf = F.intersect_closest_host(fib, case["rays"], np.zeros(n + 1, np.int32), np.zeros(0, np.int32), 8)
+    assert np.all(np.isinf(tu.numpy()[:, 0])) and np.all(tu.numpy()[:, 1] == -1)
+    assert np.all(seg.numpy() == -1) and np.all(lf.numpy() == -1)
+    one = I.subsample_rays(case, np.array([5]))
+    tu1, seg1, lf1 = F.intersect_closest_host(fib, one["rays"], one["row_ptr"], one["seg_idx"], 12)
+    tu_d, seg_d, lf_d = F.intersect_closest(fib, one["rays"], one["row_ptr"], one["seg_idx"], 12)
+    np.testing.assert_array_equal(tu1.numpy(), _np(tu_d))
+    assert seg1.numpy()[0] == 5
+    rd = np.arange(n, dtype=np.int8) % 24
+    h = F.intersect_closest_host(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8, ray_depth=rd)
+    d = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8, ray_depth=rd)
+    for a, b in zip(h, d):
+        np.testing.assert_array_equal(a.numpy(), _np(b))
+    assert fib.status() == 0
+    fib.close()
