@@ -25,9 +25,13 @@
  *    available from fx_last_error().
  *  - Device-side conditions never trap: they set bits of the handle's sticky
  *    status word (FX_DEV_*), read and cleared by fx_stream_status.
- *  - One handle may be used by several calls only in stream order (same
- *    stream, or streams ordered by events): the persistent kernels share the
- *    handle's work-queue counters.
+ *  - Calls on one handle may run concurrently on unordered streams: each
+ *    call's work-queue counter and scratch come from the handle's
+ *    stream-ordered memory pool.  They share the sticky status word and the
+ *    counters (bits and sums of all of them).  Exceptions:
+ *    intersect_closest_host (the handle's staging) and
+ *    intersect_closest_noalloc (one key array per device) must not overlap
+ *    another call of their own kind.
  */
 #ifndef FIBERX_H
 #define FIBERX_H

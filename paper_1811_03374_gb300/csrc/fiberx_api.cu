@@ -73,21 +73,9 @@ fx::TraceArgs make_args(const fx_fibers* f, const float* rays, int64_t n_ray, co
   return a;
 }
 
-fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t flags,
+// The persistent variants; a.queue is this call's work-queue counter.
+fx_status run_variant(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t flags,
                       cudaStream_t s) {
-  if (a.n_ray == 0) return FX_OK;
-  if (flags & FX_KERNEL_NAIVE) {
-    unsigned long long* scratch = nullptr;
-    if (!pairs) {
-      FX_CUDA(cudaMallocFromPoolAsync((void**)&scratch, sizeof(unsigned long long) * a.n_ray, f->pool, s));
-      FX_CUDA(cudaMemsetAsync(scratch, 0xff, sizeof(unsigned long long) * a.n_ray, s));
-    }
-    a.scratch = scratch;
-    cudaError_t e = fx::launch_naive(a, pairs, flags, s);
-    if (scratch) cudaFreeAsync(scratch, s);
-    if (e != cudaSuccess) return cuda_fail(e, "naive kernel launch");
-    return FX_OK;
-  }
   FX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s));
   int variant = f->launch.variant;
   // rows of one or two candidates on average, segments not pre-split: the
@@ -148,6 +136,32 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
     FX_CUDA(fx::launch_lane_ray(a, pairs, flags, f->launch.blocks_per_sm, f->sm_count, s));
   }
   return FX_OK;
+}
+
+fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t flags,
+                      cudaStream_t s) {
+  if (a.n_ray == 0) return FX_OK;
+  if (flags & FX_KERNEL_NAIVE) {
+    unsigned long long* scratch = nullptr;
+    if (!pairs) {
+      FX_CUDA(cudaMallocFromPoolAsync((void**)&scratch, sizeof(unsigned long long) * a.n_ray, f->pool, s));
+      FX_CUDA(cudaMemsetAsync(scratch, 0xff, sizeof(unsigned long long) * a.n_ray, s));
+    }
+    a.scratch = scratch;
+    cudaError_t e = fx::launch_naive(a, pairs, flags, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "naive kernel launch");
+    return FX_OK;
+  }
+  // each call's work-queue counter comes from the handle's pool on the
+  // call's stream, so that calls on one handle in unordered streams do not
+  // share one
+  uint32_t* queue = nullptr;
+  FX_CUDA(cudaMallocFromPoolAsync((void**)&queue, sizeof(uint32_t), f->pool, s));
+  a.queue = queue;
+  const fx_status st = run_variant(f, a, pairs, flags, s);
+  cudaFreeAsync(queue, s);
+  return st;
 }
 
 bool device_is_sm103(int dev, int* sm_count) {

@@ -590,3 +590,35 @@ def test_host_entry_edge_cases():
         np.testing.assert_array_equal(a.numpy(), _np(b))
     assert fib.status() == 0
     fib.close()
+
+
+@pytest.mark.parametrize("variant", [F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN, F.FX_VARIANT_RAY, F.FX_VARIANT_WARP,
+                                     F.FX_VARIANT_FILTER], ids=["lane", "scan", "ray", "warp", "filter"])
+def test_concurrent_calls_on_one_handle(variant):
+    # two calls on one handle in unordered streams, each several times over,
+    # give the results of the same calls one after the other
+    case = I.sweep_case("moderate", 1 << 16, forced_hits=True)
+    g = np.random.default_rng(9)
+    n = len(case["rays"])
+    rows = [np.concatenate([[i], g.integers(0, n, 12)]).astype(np.int32) for i in range(n)]
+    case2 = dict(case, seg_idx=np.concatenate(rows),
+                 row_ptr=np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32))
+    fib = F.Fibers(case["cps"])
+    fib.set_launch(variant=variant)
+    dev = [tuple(torch.from_numpy(np.asarray(c[k])).cuda() for k in ("rays", "row_ptr", "seg_idx"))
+           for c in (case, case2)]
+    ref = [tuple(_np(x) for x in F.intersect_closest(fib, *d, 14)) for d in dev]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [[], []]
+    torch.cuda.synchronize()
+    for _ in range(4):
+        for k in (0, 1):
+            with torch.cuda.stream(streams[k]):
+                outs[k].append(F.intersect_closest(fib, *dev[k], 14, stream=streams[k]))
+    torch.cuda.synchronize()
+    for k in (0, 1):
+        for o in outs[k]:
+            for a, b in zip(o, ref[k]):
+                np.testing.assert_array_equal(_np(a), b)
+    assert fib.status() == 0
+    fib.close()
