@@ -532,6 +532,9 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
 #ifndef FX_HOST_RAY_BLOCK
 #define FX_HOST_RAY_BLOCK 8192
 #endif
+#ifndef FX_HOST_LAST_SHARE
+#define FX_HOST_LAST_SHARE 25
+#endif
   constexpr int64_t kChunkBytes = (int64_t)FX_HOST_CHUNK_MB << 20;
   constexpr int64_t kRayBlock = FX_HOST_RAY_BLOCK;
   const int64_t in_bytes = 36 * n_ray + 4 * n_pair;
@@ -541,8 +544,12 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   int64_t cut[kFxHostChunks + 1];
   cut[0] = 0;
   cut[n_chunk] = n_ray;
+  // the last chunk takes FX_HOST_LAST_SHARE percent of the bytes (its
+  // kernels and copy out are the part of the step no copy in overlaps), the
+  // others share the rest evenly
+  const int64_t last_share = n_chunk > 1 ? std::min<int64_t>(FX_HOST_LAST_SHARE, 100 / n_chunk) : 100;
   for (int c = 1; c < n_chunk; ++c) {
-    const int64_t target = in_bytes * c / n_chunk;
+    const int64_t target = in_bytes * (100 - last_share) / 100 * c / (n_chunk - 1);
     int64_t lo = cut[c - 1], hi = n_ray;  // smallest r in [lo, hi] with bytes(r) >= target
     while (lo < hi) {
       const int64_t mid = lo + (hi - lo) / 2;
