@@ -622,3 +622,24 @@ def test_concurrent_calls_on_one_handle(variant):
                 np.testing.assert_array_equal(_np(a), b)
     assert fib.status() == 0
     fib.close()
+
+
+def test_host_entry_on_the_hair_frame(hair):
+    # the end-to-end path the bench times (tuned launch: scan variant, fast
+    # math, depth 15, pinned host buffers, chunked copies) equals the device
+    # entry on the full frame, and its sampled rays pass parity with the oracle
+    case, idx, sub, pieces, ref = hair
+    fib = F.Fibers(case["cps"])
+    fib.set_launch(128, 5, 4, F.FX_VARIANT_SCAN)
+    h = [torch.from_numpy(case[k]).pin_memory() for k in ("rays", "row_ptr", "seg_idx")]
+    tu_h, seg_h, leaf_h = F.intersect_closest_host(fib, *h, 15, F.FX_FAST_MATH)
+    tu_d, seg_d, leaf_d = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 15, F.FX_FAST_MATH)
+    np.testing.assert_array_equal(tu_h.numpy(), _np(tu_d))
+    np.testing.assert_array_equal(seg_h.numpy(), _np(seg_d))
+    np.testing.assert_array_equal(leaf_h.numpy(), _np(leaf_d))
+    h2d, d2h = F.host_bytes(fib)
+    assert h2d < 32 * len(case["rays"]) + 4 * (len(case["rays"]) + 1) + 4 * len(case["seg_idx"])
+    assert fib.status() == 0
+    fib.close()
+    stats = P.compare_closest(sub, 15, tu_h.numpy()[idx], seg_h.numpy()[idx], ref[15], pieces, leaf_h.numpy()[idx])
+    _assert_parity(stats, where="hair host entry")
