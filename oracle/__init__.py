@@ -210,7 +210,7 @@ def closest(case, depth, pieces=None, nthreads=0):
 
 
 def ray_counts(case, depth, mode, pieces=None, nthreads=0):
-    """Per-ray pruning tests (Fig. 8; reading R30): mode "cylinder" (the
+    """Per-ray pruning tests (Fig. 8): mode "cylinder" (the
     traversal's node tests) or "box" (ray-frame axis-aligned boxes); each ray's
     candidates in row order with the closest hit so far as t_max.  Returns
     (counts int64 [n_ray], closest t [n_ray])."""

@@ -14,8 +14,8 @@
  * subdivision rules (Sec. 3.1), the partitioned bounding cylinder (Sec. 3.2,
  * Fig. 5), the unit-ray cylinder / plane tests (Sec. 3.3, App. A), the
  * bit-string traversal (Sec. 3.3) and the curve constraints (Sec. 3.4,
- * App. B.2).  Where the paper is silent or garbled the reading taken is named
- * at the place it is used (readings R1..R19 in the design notes).
+ * App. B.2).  Where the paper is silent or garbled, the reading taken is
+ * stated at the place it is used.
  *
  * Parity of each exported function is pinned by the oracle test suite
  * (closed forms, brute force over leaves, golden values from the paper's
@@ -135,7 +135,7 @@ static ray_t make_ray_d(const double *r7)
 }
 
 /* Control points in the ray-centric frame: the ray starts at the origin and
- * runs along +z; the radius is carried unchanged (Sec. 3.3, reading R8). */
+ * runs along +z; the radius is carried unchanged (Sec. 3.3). */
 static void to_ray_frame(const ray_t *r, const double *cp, v4 Q[4])
 {
     for (int k = 0; k < 4; ++k) {
@@ -163,7 +163,7 @@ static int plane_t(v4 p, v4 n, double *t)
  * (App. A): g = a_x^2 + a_y^2, squared distance (a_x p_y - a_y p_x)^2 / g,
  * t_cpa = p_z - a_z (a_x p_x + a_y p_y) / g, s = sqrt((r^2 - d^2)(a_z^2 + g) / g),
  * hits at t_cpa -+ s.  Axis parallel to the ray (g == 0): inside gives
- * (-inf, +inf), outside is a miss (reading R3).  Returns 0 on a miss.
+ * (-inf, +inf), outside is a miss.  Returns 0 on a miss.
  */
 static int cylinder(v4 p, v4 a, double r, double *c0, double *c1)
 {
@@ -210,8 +210,8 @@ static double cons_radius(const node_t *c)
  * through p with normal t0 (kept side <x - p, t0> >= 0) and the end plane
  * through p + d with normal t1 (kept side <x - p - d, t1> <= 0), clipped to
  * [0, ray_tmax] (Sec. 3.3).  A plane parallel to the ray either leaves the
- * interval alone or, if the ray lies on its excluded side, empties it
- * (reading R4).  Returns 0 for an empty interval.
+ * interval alone or, if the ray lies on its excluded side, empties it.
+ * Returns 0 for an empty interval.
  */
 static int slab(const node_t *c, double ray_tmax, double *tmin, double *tmax)
 {
@@ -290,7 +290,7 @@ static void node_of_points(const v4 Q[4], node_t *c)
  * interval (start, size).  Each step tests the node's bounding cylinder
  * against the interval:
  *   - overlap and size <= min_size: leaf; the hit is the entry into the
- *     capped leaf cylinder, max(c0, tmin) (reading R1); stop (immediate
+ *     capped leaf cylinder, max(c0, tmin); stop (immediate
  *     termination, Sec. 3.2);
  *   - overlap otherwise: partition by the plane through the split point with
  *     normal tc, continue with the child the ray reaches first, tighten one
@@ -299,7 +299,7 @@ static void node_of_points(const v4 Q[4], node_t *c)
  *   - no overlap: if no bit is set, stop; otherwise jump to the sibling at the
  *     deepest set bit and recompute its node and interval.
  * Overlap means the cylinder is hit and max(c0, tmin) <= min(c1, tmax): the
- * listing's comparisons plus non-emptiness of both intervals (reading R5).
+ * listing's comparisons plus non-emptiness of both intervals.
  */
 static void traverse(const v4 Q[4], int depth, double ray_tmax, orc_hit *h)
 {
@@ -332,7 +332,7 @@ static void traverse(const v4 Q[4], int depth, double ray_tmax, orc_hit *h)
                 if (tp > c0) tmax = dmin(tmax, tp);
                 else tmin = dmax(tmin, tp);
             } else {
-                /* plane parallel to the ray: the ray stays on the origin's side (R4) */
+                /* plane parallel to the ray: the ray stays on the origin's side */
                 go_right = -dot3(s, tc) >= 0.0;
                 both = 0;
             }
@@ -481,7 +481,7 @@ static int nonneg01(poly_t x)
  * both must be non-negative on [0, 1] (at u = 1 the second reduces to
  * rbar * curvature <= 1).  The start plane through p0 with normal p1 - p0
  * likewise, roots at u = 0.  The paper speaks of a quartic; these are the
- * same conditions checked exactly on the polynomials (reading R13).
+ * same conditions, checked exactly on the polynomials.
  * Returns 1 if neither end plane crops the fiber.
  */
 int orc_thick_ok(const double *cp)
@@ -555,7 +555,7 @@ void orc_split_half(const double *cp, double *L, double *R)
 
 /*
  * Pre-split (Sec. 3.4: a curve violating the constraints has to be split before it
- * is traversed; reading R15): a curve failing the constraints or the
+ * is traversed): a curve failing the constraints or the
  * thick-fiber check is halved at u = 1/2, recursively, left before right, up
  * to max_level levels.  A piece still failing at max_level is kept and
  * flagged unsupported (flag bit 0).
@@ -616,7 +616,7 @@ int64_t orc_presplit_d(const double *cps, int64_t n_seg, int max_level, int thic
 
 /*
  * Fig. 8 compares the number of pruning tests of the oriented bounding
- * cylinders with axis-aligned boxes in the ray's frame (reading R30; the
+ * cylinders with axis-aligned boxes in the ray's frame (the
  * boxes in Duff et al.'s frame, below).  Per
  * ray, each candidate is searched in row order with the closest hit so far
  * as t_max, with no test before the root's, so that only the bounding volume
@@ -784,7 +784,7 @@ void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, co
  * <p1 - p0, p1 - p2> <= 0 (positions).  (The lemma claims an equivalence,
  * but its two one-sided conditions <p1 - p0, p2 - p0> >= 0 and
  * <p1 - p2, p0 - p2> >= 0 do not imply the combined one; the combined one is
- * the one its second lemma carries to every subcurve.  Reading R29.)
+ * the one its second lemma carries to every subcurve.)
  */
 int orc_valid_quadratic(const double *cp12)
 {
@@ -797,7 +797,7 @@ int orc_valid_quadratic(const double *cp12)
  * curve and parametrisation (all four components, radius included):
  * q0 = p0, q1 = (p0 + 2 p1) / 3, q2 = (2 p1 + p2) / 3, q3 = p2.  The method's
  * representation and subdivision rules (Sec. 3.1) are stated for cubics; a
- * quadratic fiber is intersected as its raised cubic (reading R29).
+ * quadratic fiber is intersected as its raised cubic.
  */
 void orc_elevate_quadratic(const double *cp12, double *cp16)
 {
@@ -825,7 +825,7 @@ static int piece_depth(int depth, int level) { return depth > level ? depth - le
 
 /*
  * One candidate segment against a ray: its pieces in order, each traversed to
- * depth - level (reading R15); the pieces' best hit (ties keep the earlier
+ * depth - level; the pieces' best hit (ties keep the earlier
  * piece, so a piece is tested with the best t of the earlier pieces as t_max).
  * Returns 1 on a hit closer than tmax; u and leaf refer to the segment.
  */
@@ -1062,10 +1062,10 @@ int orc_leaf_hit(const double *ray7, const double *cp, int depth, uint32_t leaf,
  *     point minus a, taken back to world space (x e1 + y e2 + z w) and
  *     normalised.
  * (The listing's cur_c.axis and ray_direction are the leaf's d and the ray
- * direction w; reading R9.)  The listing takes u == 0 or u == 1 for an end
+ * direction w.)  The listing takes u == 0 or u == 1 for an end
  * cap; a hit on an end disk projects onto the leaf axis a rounding away from
  * either side of u_local = 0, so that test classifies end-disk hits by their
- * rounding.  Reading R28: the hit is on the cap at u = 0 (u = 1) if its leaf
+ * rounding.  Here the hit is on the cap at u = 0 (u = 1) if its leaf
  * is the first (last) one and the hit point lies on or beyond the segment's
  * end plane through p0 with normal p1 - p0 (through p3, normal p3 - p2), to
  * within 1e-12 (t + |p0|) here in FP64.  Writes n3 and returns 1 for a
@@ -1120,7 +1120,7 @@ int orc_normal(const double *ray7, const double *cp, uint32_t start, uint32_t si
 
 /*
  * The surface the leaf cylinders converge to as the depth grows (Sec. 3.2:
- * the cylinders' limit surface; reading R19): circles of radius r(u) in the
+ * the cylinders' limit surface): circles of radius r(u) in the
  * plane through c(u) normal to c'(u), closed by the flat end disks at u = 0
  * and u = 1.  With x = o + t w:
  *   G1(t, u) = <x - c(u), c'(u)> = 0,   G2(t, u) = |x - c(u)|^2 - r(u)^2 = 0.
@@ -1210,7 +1210,7 @@ int orc_limit_hit(const double *ray7, const double *cp, int n_grid, double *t_ou
 }
 
 /*
- * dt / d(p_k, r_k) at a hit of the limit surface (reading R19), by the
+ * dt / d(p_k, r_k) at a hit of the limit surface, by the
  * implicit function theorem on G(t, u; theta) = 0:
  *   [dt, du]^T = -J^{-1} dG/dtheta,  J = dG/d(t, u),
  *   dG1/dp_k = -B_k c' + B_k' (x - c),  dG2/dp_k = -2 B_k (x - c),

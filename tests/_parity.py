@@ -202,7 +202,7 @@ def pairs_min(pr, case):
 
 def report(rec):
     """Appends one JSON line to the file named by FX_REPORT, if set (the
-    figures a run measured, for the design notes)."""
+    figures a run measured)."""
     path = os.environ.get("FX_REPORT")
     if path:
         with open(path, "a") as f:

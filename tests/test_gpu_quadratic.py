@@ -1,6 +1,6 @@
 """Quadratic fibers on the GPU (fiber_upload_quadratic: exact degree
 elevation, then the cubic path) against the FP64 oracle, which raises the
-same FP32 control points in FP64 (reading R29): the depth-sweep classes,
+same FP32 control points in FP64: the depth-sweep classes,
 forced hits and box-aimed rays, IEEE and fast math, depths 2-22, and the
 adjoint through the autograd Function against FP64 central finite
 differences on the quadratic control points."""

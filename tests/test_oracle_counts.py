@@ -1,4 +1,4 @@
-"""Pins of the oracle's pruning-test statistic (Fig. 8; reading R30): the
+"""Pins of the oracle's pruning-test statistic (Fig. 8): the
 cylinder counts are the traversal's node tests, the box search finds the same
 hits, hand-counted box cases, and the figure's claim that box tests grow
 exponentially with the depth while cylinder tests grow by about one per level

@@ -1,6 +1,6 @@
 """Pins of the oracle's hit normal (App. C: the hit point minus its
 projection onto the hit leaf's axis, or the outward end-disk normal for a
-hit on an end disk -- one on or beyond the segment's end plane, reading R28)
+hit on an end disk -- one on or beyond the segment's end plane)
 against closed forms, the limit surface and invariants (CPU only)."""
 import numpy as np
 import pytest

@@ -109,7 +109,7 @@ def test_unit_ray_cylinder_matches_world_solve(seed):
 
 
 def test_unit_ray_cylinder_axis_parallel_to_ray():
-    # App. A special case g = 0: distance is |p_xy| (reading R3 outside).
+    # App. A special case g = 0: distance is |p_xy|; outside, a miss.
     assert O.cylinder([0.1, 0.0, 3.0], [0, 0, 2.0], 0.2) == (-np.inf, np.inf)
     assert O.cylinder([0.3, 0.0, 3.0], [0, 0, 2.0], 0.2) is None
 
@@ -153,7 +153,7 @@ def test_slab_is_region_between_end_planes(seed):
 
 
 def test_slab_plane_parallel_to_ray():
-    # reading R4: a plane parallel to the ray constrains nothing unless the
+    # a plane parallel to the ray constrains nothing unless the
     # ray is on its excluded side, which empties the interval.
     node = np.array([[0, 0, 1, 0], [0, 0, 2, 0], [1, 0, 0, 0], [0, 0, 1, 0]], float)
     node[0, 0] = -0.5  # start plane x = -0.5 with normal +x: origin kept
@@ -212,7 +212,7 @@ def test_lemma_valid_halves_are_separated_by_split_plane(seed):
 
 
 def test_presplit_pieces_tile_each_segment():
-    # reading R15: pieces are dyadic sub-curves covering [0, 1] in order.
+    # pieces are dyadic sub-curves covering [0, 1] in order.
     from paper_1811_03374_gb300 import inputs as I
     case = I.tiny_case()
     pc = O.presplit(case["cps"])

@@ -1,5 +1,5 @@
 """Pins of the oracle's quadratic fibers (App. B.1 constraint; intersection
-as the raised cubic, reading R29) against closed forms, brute force and the
+as the raised cubic) against closed forms, brute force and the
 paper's figure (CPU only)."""
 import os
 
@@ -84,7 +84,7 @@ def test_constraint_separates_the_halves_and_is_kept_by_them():
 
 
 def test_constraint_is_sufficient_not_necessary():
-    # reading R29: halves can be separated while the constraint fails (the
+    # halves can be separated while the constraint fails (the
     # lemma's one-sided conditions do not combine into it)
     q = np.array([[0.0, 0, 0, 0], [1.0, 0, 0, 0], [0.5, 1, 0, 0]])
     assert not O.valid_quadratic(q)

@@ -1,5 +1,5 @@
-"""Pins of the oracle's end-plane check for thick fibers (Sec. 3.4, Fig. 7;
-reading R13): the exact polynomial criterion against dense sampling of the
+"""Pins of the oracle's end-plane check for thick fibers (Sec. 3.4, Fig. 7):
+the exact polynomial criterion against dense sampling of the
 distance the cross-sections keep from the end planes, straight fibers of any
 radius, monotonicity in the radius, and the end-curvature limit (CPU only)."""
 import numpy as np
