@@ -643,3 +643,17 @@ def test_host_entry_on_the_hair_frame(hair):
     fib.close()
     stats = P.compare_closest(sub, 15, tu_h.numpy()[idx], seg_h.numpy()[idx], ref[15], pieces, leaf_h.numpy()[idx])
     _assert_parity(stats, where="hair host entry")
+
+
+def test_upload_from_device_memory_equals_host_upload(tiny):
+    # fiber_upload with cps_on_device = 1 (a CUDA tensor) makes the same
+    # handle as from host memory: same pieces, same results
+    case, _, _ = tiny
+    fh = F.Fibers(case["cps"])
+    fd = F.Fibers(torch.from_numpy(case["cps"]).cuda())
+    assert fh.info() == fd.info()
+    args = (case["rays"], case["row_ptr"], case["seg_idx"], 12)
+    for a, b in zip(F.intersect_closest(fh, *args), F.intersect_closest(fd, *args)):
+        np.testing.assert_array_equal(_np(a), _np(b))
+    fh.close()
+    fd.close()
