@@ -145,7 +145,11 @@ fx_status run_forward(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
     unsigned long long* scratch = nullptr;
     if (!pairs) {
       FX_CUDA(cudaMallocFromPoolAsync((void**)&scratch, sizeof(unsigned long long) * a.n_ray, f->pool, s));
-      FX_CUDA(cudaMemsetAsync(scratch, 0xff, sizeof(unsigned long long) * a.n_ray, s));
+      const cudaError_t e0 = cudaMemsetAsync(scratch, 0xff, sizeof(unsigned long long) * a.n_ray, s);
+      if (e0 != cudaSuccess) {
+        cudaFreeAsync(scratch, s);
+        return cuda_fail(e0, "naive kernel keys");
+      }
     }
     a.scratch = scratch;
     cudaError_t e = fx::launch_naive(a, pairs, flags, s);
