@@ -66,7 +66,7 @@ typedef enum {
 #define FX_FAST_MATH 0x2u         /* approximate reciprocal / square root in the traversal */
 #define FX_POLISH_FP64 0x4u       /* re-evaluate each hit's leaf and its neighbours in FP64, keep the nearest (intersect_closest) */
 #define FX_COUNT 0x8u             /* accumulate node / descent / backtrack counters */
-#define FX_CHECK_INDEX 0x10u      /* range-check candidate segment ids on the device */
+#define FX_CHECK_INDEX 0x10u      /* range-check candidate segment ids and rows on the device */
 #define FX_COUNT_BOXES 0x20u      /* intersect_counts: ray-frame axis-aligned boxes instead of cylinders */
 
 typedef struct fx_fibers fx_fibers; /* opaque; owns the device copy of the fibers */
@@ -176,7 +176,9 @@ fx_status fiber_info(const fx_fibers *f, fx_fibers_info *out);
  * row_ptr: n_ray + 1 int32 (row_ptr[0] = 0, non-decreasing, row_ptr[n_ray] =
  * n_pair); seg_idx: n_pair int32 segment ids.  The CSR is validated on the
  * host only for its sizes; set FX_CHECK_INDEX to range-check ids on the
- * device.
+ * device and to clamp each row to [0, n_pair], non-decreasing (both flagged
+ * FX_DEV_BAD_INDEX), so that a malformed CSR reads nothing out of range; the
+ * filter and warp variants then run as the lane kernel.
  * depth: subdivision depth d in [0, 23]; leaves have size 2^-d (Sec. 3.3:
  * termination after a fixed number of subdivisions).
  * ray_depth: nullable; n_ray int8 per-ray depths (device pointer) that

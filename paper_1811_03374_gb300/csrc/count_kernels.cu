@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kCountBlock) k_counts(const TraceArgs a, uint3
                                                         int check) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.n_ray) return;
-  const int32_t crow = __ldg(a.row_ptr + r), cend = __ldg(a.row_ptr + r + 1);
+  int32_t crow = __ldg(a.row_ptr + r), cend = __ldg(a.row_ptr + r + 1);
+  if (check) clamp_row(a, crow, cend);
   uint64_t n = 0;
   if (crow < cend) {
     float ray_tmax;

@@ -86,6 +86,11 @@ fx_status run_variant(const fx_fibers* f, fx::TraceArgs& a, bool pairs, uint32_t
     variant = (a.n_pair <= 2 * a.n_ray && f->identity) ? FX_VARIANT_RAY : FX_VARIANT_LANE;
   // the two-phase path covers closest hits on handles of single level-0 pieces
   if (variant == FX_VARIANT_FILTER && (pairs || !f->identity)) variant = FX_VARIANT_LANE;
+  // FX_CHECK_INDEX also guards against a malformed row_ptr (rows clamped to
+  // [0, n_pair]); the filter and warp variants stream several rows as one
+  // range and rely on a well-formed CSR, so the lane kernel runs instead
+  if ((flags & FX_CHECK_INDEX) && (variant == FX_VARIANT_FILTER || variant == FX_VARIANT_WARP))
+    variant = FX_VARIANT_LANE;
   // the scan path covers handles of single level-0 pieces
   if (variant == FX_VARIANT_SCAN && !f->identity) variant = FX_VARIANT_LANE;
   if (variant == FX_VARIANT_FILTER) {

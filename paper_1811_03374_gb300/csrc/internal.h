@@ -89,6 +89,16 @@ __device__ __forceinline__ int depth_of(const TraceArgs &a, int64_t r) {
   }
   return d;
 }
+// With FX_CHECK_INDEX, a row of the CSR is clamped to [0, n_pair] and made
+// non-decreasing (FX_DEV_BAD_INDEX when it had to be), so that a malformed
+// row_ptr makes no kernel read or write out of range.
+__device__ __forceinline__ void clamp_row(const TraceArgs &a, int32_t &crow, int32_t &cend) {
+  const int32_t n = (int32_t)a.n_pair;
+  const int32_t c0 = min(max(crow, 0), n), c1 = min(max(cend, c0), n);
+  if (c0 != crow || c1 != cend) atomicOr(a.status, FX_DEV_BAD_INDEX);
+  crow = c0;
+  cend = c1;
+}
 // Iteration cap of one (ray, piece) test at a depth: a guard against runaway
 // loops, far above any depth's node count.  (Compile-time settings, so that
 // a test build can make the guard trip.)

@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
         const int64_t r = pool_next + rank;
         crow = __ldg(a.row_ptr + r);
         cend = __ldg(a.row_ptr + r + 1);
+        if (check) clamp_row(a, crow, cend);
         if (crow >= cend) {
           if (!PAIRS) {  // no candidates: a miss, without loading the ray
             a.tu[r] = make_float2(kInf, -1.0f);

@@ -90,7 +90,8 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
       cnt[4] += n_hits;
     }
   };
-  const int32_t crow = __ldg(a.row_ptr + r), cend = __ldg(a.row_ptr + r + 1);
+  int32_t crow = __ldg(a.row_ptr + r), cend = __ldg(a.row_ptr + r + 1);
+  if (check) clamp_row(a, crow, cend);
   float ray_tmax = 0.0f, best_t = 0.0f, best_u = -1.0f;
   int32_t best_seg = -1, best_leaf = -1;
   RayFrame rf{};

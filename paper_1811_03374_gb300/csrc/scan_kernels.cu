@@ -106,7 +106,7 @@ __device__ __forceinline__ float bound_lhs(float zp, float zd, float rb) {
 // hit) and are written here; the others are appended to o.act, 32
 // consecutive rays of a warp as one group (one atomic per warp).
 template <bool PAIRS>
-__global__ void __launch_bounds__(256) k_rows(const TraceArgs a, const ScanArgs o) {
+__global__ void __launch_bounds__(256) k_rows(const TraceArgs a, const ScanArgs o, int check) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < a.n_ray; r0 += stride) {
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(256) k_rows(const TraceArgs a, const ScanArgs 
     if (r < a.n_ray) {
       crow = __ldg(a.row_ptr + r);
       cend = __ldg(a.row_ptr + r + 1);
+      if (check) clamp_row(a, crow, cend);
     }
     const bool has = crow < cend;
     if (r < a.n_ray && !has && !PAIRS) {
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
 
 template <bool FAST, bool PAIRS, bool COUNT>
 cudaError_t launch_s(const TraceArgs& a, const ScanArgs& o, int check, int bps_cap, int sms, cudaStream_t s) {
-  k_rows<PAIRS><<<sms * 8, 256, 0, s>>>(a, o);
+  k_rows<PAIRS><<<sms * 8, 256, 0, s>>>(a, o, check);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int occ = 0;

@@ -657,3 +657,43 @@ def test_upload_from_device_memory_equals_host_upload(tiny):
         np.testing.assert_array_equal(_np(a), _np(b))
     fh.close()
     fd.close()
+
+
+@pytest.mark.parametrize("variant,kernel", [(F.FX_VARIANT_LANE, 0), (F.FX_VARIANT_SCAN, 0), (F.FX_VARIANT_RAY, 0),
+                                            (F.FX_VARIANT_WARP, 0), (F.FX_VARIANT_FILTER, 0),
+                                            (0, F.FX_KERNEL_NAIVE)],
+                         ids=["lane", "scan", "ray", "warp", "filter", "naive"])
+def test_malformed_row_ptr_is_clamped_under_check_index(variant, kernel):
+    # with FX_CHECK_INDEX a row_ptr with negative, too large and decreasing
+    # entries reads nothing out of range: the bad rows are clamped to
+    # [0, n_pair] and flagged, and every other ray's result is unchanged
+    case = I.sweep_case("moderate", 4096, forced_hits=True)
+    n = len(case["rays"])
+    g = np.random.default_rng(13)
+    rows = [np.concatenate([[i], g.integers(0, n, 3)]).astype(np.int32) for i in range(n)]
+    seg_idx = np.concatenate(rows)
+    good = (np.arange(n + 1) * 4).astype(np.int32)
+    bad = good.copy()
+    n_pair = len(seg_idx)
+    bad[100] = -7
+    bad[200] = n_pair + 50
+    bad[300] = bad[299] - 3
+    bad[n] = n_pair + 10
+    touched = np.zeros(n, bool)
+    touched[[99, 100, 199, 200, 299, 300, n - 1]] = True
+    fib = F.Fibers(case["cps"])
+    fib.set_launch(variant=variant)
+    flags = kernel | F.FX_CHECK_INDEX
+    ref = [_np(x) for x in F.intersect_closest(fib, case["rays"], good, seg_idx, 12, flags)]
+    assert fib.status() == 0
+    got = [_np(x) for x in F.intersect_closest(fib, case["rays"], bad, seg_idx, 12, flags)]
+    st = fib.status()
+    if kernel == 0:  # the naive kernel maps pairs to rays and reads no row as such
+        assert st & F.FX_DEV_BAD_INDEX
+    assert st & ~F.FX_DEV_BAD_INDEX == 0
+    if kernel == 0:  # the row kernels keep every other ray's result (the naive
+        # kernel's pair-to-ray search assumes a sorted row_ptr)
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a[~touched], b[~touched])
+    assert np.all((got[1] >= -1) & (got[1] < n))
+    fib.close()
