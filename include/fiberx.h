@@ -57,7 +57,7 @@ typedef enum {
 /* Sticky device status bits (fx_stream_status). */
 #define FX_DEV_ITER_LIMIT 0x1u  /* a (ray, segment) test hit the per-pair iteration cap */
 #define FX_DEV_UNSUPPORTED 0x2u /* a hit was reported on a piece flagged unsupported */
-#define FX_DEV_BAD_INDEX 0x4u   /* a candidate segment id was out of range (skipped) */
+#define FX_DEV_BAD_INDEX 0x4u   /* a segment id was out of range (skipped), or with FX_CHECK_INDEX a CSR row (clamped) */
 #define FX_DEV_BAD_DEPTH 0x8u   /* a per-ray depth was outside [0, 23] (clamped to it) */
 
 /* intersect_* flags */
