@@ -66,3 +66,16 @@ def test_python_binding_has_no_cpu_fallback():
     case = inputs.tiny_case(n_ray=4)
     with pytest.raises(Exception):
         F.Fibers(case["cps"])
+
+
+def test_product_never_loads_the_oracle():
+    # the package and its C sources share nothing with oracle/: no import,
+    # no include, no link (only tests, smoke() and bench.py's CPU legs use it)
+    pkg = os.path.join(ROOT, "paper_1811_03374_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if not name.endswith((".py", ".cu", ".cuh", ".cpp", ".h", ".c")):
+                continue
+            src = open(os.path.join(dirpath, name), encoding="utf-8").read()
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), name
+            assert "fiber_oracle" not in src and "oracle/" not in src, name
