@@ -79,3 +79,17 @@ def test_product_never_loads_the_oracle():
             src = open(os.path.join(dirpath, name), encoding="utf-8").read()
             assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), name
             assert "fiber_oracle" not in src and "oracle/" not in src, name
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 on its own
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "fiberx.h"\nint main(void) { return fx_version() > 0 ? 0 : 1; }\n')
+    r = subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
