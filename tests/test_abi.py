@@ -93,3 +93,18 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_library_depends_on_no_framework():
+    # the shared library stands alone: the CUDA runtime is linked in, and it
+    # needs no PyTorch, Python or other framework library to load
+    import shutil
+    import subprocess
+    if shutil.which("readelf") is None:
+        pytest.skip("no readelf")
+    F.lib()
+    out = subprocess.run(["readelf", "-d", F.library_path()], capture_output=True, text=True).stdout
+    needed = re.findall(r"\(NEEDED\)\s+Shared library: \[([^\]]+)\]", out)
+    assert needed
+    for lib_name in needed:
+        assert not re.search(r"torch|c10|python|triton", lib_name), lib_name
