@@ -1,36 +1,56 @@
 """Element-wise comparison of the CUDA path with the FP64 oracle.
 
-A ray passes when hit/miss agree and, for hits, the segment is the same,
+A result (one ray's closest hit, or one pair's hit) passes STRICT when
+hit/miss agree and, for hits, the segment is the same,
 |t - t_ref| <= TOL_T * t_ref and |u - u_ref| <= tol_u (the stated tolerance:
-relative t error <= 1e-5, |u error| <= 1e-5).  tol_u is 1e-5 unless FP32
-cannot resolve it: a hit point carries an error of a few units in the last
-place of the distances involved, 8 * 2^-24 * (|o| + t) along the ray, which
-in the curve's parameter is that length over the parametric speed |c'(u)|;
-tol_u = max(1e-5, 8 * 2^-24 * (|o| + t) / |c'(u)|).  For short fibers seen
-from afar (the hair patch: 0.02-long segments four units away) this is
-about 2e-5; for the tiny and depth-sweep workloads it stays 1e-5.
+relative t error <= 1e-5, |u error| <= 1e-5).
 
-Rays that fail this strict rule are re-run through the oracle with the ray
-shifted sideways (8 directions orthogonal to it) by the resolution band
-    delta = 1e-4 r + 8 * 2^-24 * (|o| + t):
+FP32 resolution.  Every decision the kernels take (a cylinder's silhouette,
+a split plane, an end plane) is taken on ray-frame coordinates
+x = R (p - o) of points p of the segment, with R the ray's orthonormal
+frame.  Let T be the largest distance |p_k - o| of the segment's control
+points from the ray origin (FP64), and u = 2^-24.  The FP32 kernels form
+these coordinates with the following worst-case errors (IEEE operations
+round to nearest, relative error <= u each; the approximate forms of
+FX_FAST_MATH stay within 2.3u where they are used):
+  - p - o: one rounding of each component, <= u T;
+  - the direction w, normalised by 1 / sqrt(w.w): the common factor only
+    scales w (|w| = 1 + eta, |eta| <= 3.5u); the rounding of each product
+    turns it by at most u, i.e. <= u T sideways at distance T;
+  - the frame of Duff et al. built from that w: e1 and e2 carry absolute
+    errors <= 5.4u per vector (a = -1 / (s + w_z) <= 2u relative,
+    b = w_x w_y a <= 4u, 1 + s w_x^2 a <= 5u), and the construction is
+    orthogonal to w only up to 2 |eta| <= 7u: together <= 12.4u T sideways;
+  - the rotation, three products summed by two FMAs: <= 3u T per coordinate;
+  - the plane tests (split and end planes) add a dot product of the plane
+    normal with a point at distance <= T, <= 3u T of offset, and the split
+    point p + dp adds one rounding of p_z, <= u T.
+So a decision is the exact decision for a ray displaced sideways by at most
+    K_FRAME * u * T,  K_FRAME = 22 (1 + 1 + 12.4 + 3 + 3 + 1, rounded up);
+subdivision adds errors relative to the node's own size, far below this.
+The parameter u of a hit inherits the error of the hit position along the
+leaf axis, so tol_u = max(1e-5, K_FRAME u T / |c'(u)|): about 2e-5 for the
+hair patch (0.02-long segments four units away), 1e-5 for the tiny and
+depth-sweep workloads.
+
+Results that fail STRICT are re-run through the oracle with the ray shifted
+sideways (8 directions orthogonal to it, passed in double precision) by
+    delta * 2^-k, k = 0..16,   delta = 1e-4 r + K_FRAME * u * T:
 1e-4 r is the silhouette band within which hit/miss may differ, the second
-term is the spacing of FP32 coordinates along the ray, below which no FP32
-computation can resolve a decision (a silhouette, a split plane, an end
-plane) or place a hit (for a ray nearly parallel to a fiber a sideways
-error e moves the hit along the fiber by e / tan(angle)).  A ray passes "in
-band" if the oracle result of one shifted copy (shifts of delta * 2^-k,
-k = 0..16, in 8 directions; the shifted rays are passed in double precision)
-meets the strict rule.  The small shifts matter far from the origin: there
-the difference of a control point and a ray origin is exact in FP32 and the
-decisions are resolved far below the |o| term of delta, yet a ray nearly
-parallel to a fiber still moves its hit along the fiber by (its sideways
-error) / tan(angle).
+term the FP32 resolution above.  A result passes BAND if the oracle result
+of one shifted copy meets the strict rule.  The small shifts matter because
+near a silhouette the result moves like the square root of the shift, and
+for a ray nearly parallel to a fiber a sideways error e moves the hit along
+the fiber by e / tan(angle).  The smallest passing shift is recorded, in
+units of u T ("band_shift_uT"): it bounds the perturbation the FP32 result
+actually needed.
 
-Finally a ray is exempt ("silhouette") if it passes within 1e-4 r of the
-silhouette of the leaf cylinder hit by either side: |dist(ray, leaf axis) -
-r_leaf| < 1e-4 r_leaf, measured in FP64 between the ray line and the leaf's
-axis line.  There the hit is ill-conditioned (grazing) and hit/miss, t and u
-may all legitimately differ.  Every other ray is a failure.
+Finally a result is exempt (SILHOUETTE) if the ray passes within 1e-4 r of
+the silhouette of the leaf cylinder hit by either side:
+|dist(ray, leaf axis) - r_leaf| < 1e-4 r_leaf, in FP64 between the ray line
+and the leaf's axis line.  There the hit is ill-conditioned (grazing) and
+hit/miss, t and u may all legitimately differ.  Every other result is a
+failure.
 """
 import json
 import os
@@ -40,25 +60,47 @@ import numpy as np
 import oracle as O
 
 TOL_T = 1e-5
-P_TOL_T = TOL_T
 TOL_U = 1e-5
 EPS32 = 2.0 ** -24
+K_FRAME = 22.0
+SCALES = tuple(2.0 ** -k for k in range(17))
 
 
-def u_tolerance(case, rays, seg, t, u):
-    """Per-ray |u| tolerance (see module docstring)."""
+def _bez(cp, u):
+    u = np.clip(u, 0, 1)[:, None]
+    v = 1 - u
+    return v ** 3 * cp[:, 0] + 3 * u * v * v * cp[:, 1] + 3 * u * u * v * cp[:, 2] + u ** 3 * cp[:, 3]
+
+
+def _speed(cp, u):
+    u = np.clip(u, 0, 1)[:, None]
+    v = 1 - u
+    d = 3 * (v * v * (cp[:, 1, :3] - cp[:, 0, :3]) + 2 * u * v * (cp[:, 2, :3] - cp[:, 1, :3])
+             + u * u * (cp[:, 3, :3] - cp[:, 2, :3]))
+    return np.linalg.norm(d, axis=1)
+
+
+def frame_extent(cps, rays8, seg):
+    """T per result: the largest distance of segment seg's control points
+    from the ray origin (FP64); 0 where seg < 0."""
+    T = np.zeros(len(seg))
+    ok = seg >= 0
+    if ok.any():
+        cp = cps[seg[ok]].astype(np.float64)[:, :, :3]
+        o = rays8[ok, :3].astype(np.float64)[:, None, :]
+        T[ok] = np.linalg.norm(cp - o, axis=2).max(axis=1)
+    return T
+
+
+def u_tolerance(case, rays8, seg, t, u):
+    """Per-result |u| tolerance: max(1e-5, K_FRAME 2^-24 T / |c'(u)|)."""
+    seg = np.asarray(seg, dtype=np.int64)
     tol = np.full(len(seg), TOL_U)
     hit = (seg >= 0) & np.isfinite(t)
     if hit.any():
         cp = case["cps"][seg[hit]].astype(np.float64)
-        uu = np.clip(u[hit], 0, 1)[:, None]
-        v = 1 - uu
-        d = 3 * (v * v * (cp[:, 1, :3] - cp[:, 0, :3]) + 2 * uu * v * (cp[:, 2, :3] - cp[:, 1, :3])
-                 + uu * uu * (cp[:, 3, :3] - cp[:, 2, :3]))
-        speed = np.linalg.norm(d, axis=1)
-        o = np.linalg.norm(rays[hit, :3].astype(np.float64), axis=1)
-        res = 8 * EPS32 * (o + t[hit]) / np.maximum(speed, 1e-30)
-        tol[hit] = np.maximum(TOL_U, res)
+        T = frame_extent(case["cps"], rays8[hit], seg[hit])
+        tol[hit] = np.maximum(TOL_U, K_FRAME * EPS32 * T / np.maximum(_speed(cp, u[hit]), 1e-30))
     return tol
 
 
@@ -71,14 +113,6 @@ def strict_ok(t_g, u_g, s_g, t_o, u_o, s_o, tol_u=TOL_U):
     return ok & (~both | vals)
 
 
-def _radius_at(cps, seg, u):
-    cp = cps[seg].astype(np.float64)
-    u = np.clip(u, 0, 1)[:, None]
-    v = 1 - u
-    B = np.concatenate([v ** 3, 3 * u * v * v, 3 * u * u * v, u ** 3], axis=1)
-    return np.sum(B * cp[:, :, 3], axis=1)
-
-
 def _perp(w):
     a = np.where(np.abs(w[:, :1]) < 0.9, np.array([[1.0, 0, 0]]), np.array([[0.0, 1, 0]]))
     e1 = a - np.sum(a * w, axis=1, keepdims=True) * w
@@ -87,51 +121,60 @@ def _perp(w):
     return e1, e2
 
 
-SCALES = tuple(2.0 ** -k for k in range(17))
-
-
-def band_check(case, idx, t_g, u_g, s_g, depth, pieces, mode="closest"):
-    """Indices (subset of idx) whose GPU result the oracle reproduces for a
-    sideways-shifted copy of the ray: shifts of delta * 2^-k (k = 0..16) in
-    8 directions orthogonal to the ray.  Near a silhouette the result moves
-    like the square root of the shift, so several magnitudes are tried."""
-    if len(idx) == 0:
-        return np.zeros(0, dtype=np.int64)
-    rays = case["rays"][idx].astype(np.float64)
-    o, w = rays[:, :3], rays[:, 4:7]
+def band_check(case, rays8, cands, g, o, depth, pieces):
+    """For results that failed the strict rule: rays8 [m, 8] their rays,
+    cands a list of m candidate-id arrays (a ray's row, or one pair's
+    segment), g / o dicts of the GPU / oracle results (t, u, seg) per
+    result.  Returns (passed [m] bool, smallest passing shift in units of
+    2^-24 T [m], inf where none)."""
+    m = len(cands)
+    if m == 0:
+        return np.zeros(0, bool), np.zeros(0)
+    rays = rays8.astype(np.float64)
+    o_, w = rays[:, :3], rays[:, 4:7]
     w = w / np.linalg.norm(w, axis=1, keepdims=True)
-    t_ref = np.where(np.isfinite(t_g[idx]), t_g[idx], 0.0)
-    seg = np.where(s_g[idx] >= 0, s_g[idx], 0)
-    r = _radius_at(case["cps"], seg, u_g[idx])
-    r = np.where(s_g[idx] >= 0, r, case["cps"][:, :, 3].max())
-    delta = 1e-4 * r + 8 * EPS32 * (np.linalg.norm(o, axis=1) + t_ref)
+    # the segment and u the band is measured at: the GPU's hit, else the oracle's
+    use_g = g["seg"] >= 0
+    seg = np.where(use_g, g["seg"], o["seg"]).astype(np.int64)
+    uu = np.where(use_g, g["u"], o["u"])
+    has = seg >= 0
+    r = np.full(m, case["cps"][:, :, 3].max())
+    T = np.zeros(m)
+    if has.any():
+        r[has] = _bez(case["cps"][seg[has]].astype(np.float64), uu[has])[:, 3]
+        T[has] = frame_extent(case["cps"], rays8[has], seg[has])
+    T = np.where(has, T, np.linalg.norm(o_, axis=1))
+    delta = 1e-4 * r + K_FRAME * EPS32 * T
     e1, e2 = _perp(w)
-    dirs = [e1, -e1, e2, -e2, (e1 + e2) / np.sqrt(2), (e1 - e2) / np.sqrt(2),
-            (-e1 + e2) / np.sqrt(2), (-e1 - e2) / np.sqrt(2)]
-    shifts = [sc * dv for sc in SCALES for dv in dirs]
-    rp = case["row_ptr"].astype(np.int64)
-    cand = [case["seg_idx"][rp[i]:rp[i + 1]] for i in idx]
+    s2 = np.sqrt(0.5)
+    dirs = [e1, -e1, e2, -e2, s2 * (e1 + e2), s2 * (e1 - e2), s2 * (-e1 + e2), s2 * (-e1 - e2)]
     tmax = rays[:, 3]
     sub_rays, rows, segs = [], [0], []
-    for sh in shifts:
-        # double-precision rays: shifts far below an FP32 step of |o| stay exact
-        sub_rays.append(np.concatenate([o + delta[:, None] * sh, w, tmax[:, None]], axis=1))
-        for c in cand:
-            segs.append(c)
-            rows.append(rows[-1] + len(c))
+    for sc in SCALES:
+        for dv in dirs:
+            # double-precision rays: shifts far below an FP32 step of |o| stay exact
+            sub_rays.append(np.concatenate([o_ + (delta * sc)[:, None] * dv, w, tmax[:, None]], axis=1))
+            for c in cands:
+                segs.append(c)
+                rows.append(rows[-1] + len(c))
     ref = O.closest_d(np.concatenate(sub_rays), np.array(rows, dtype=np.int32),
                       np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32),
                       depth, pieces)
-    m = len(idx)
-    tol_u = u_tolerance(case, case["rays"][idx], s_g[idx], t_g[idx], u_g[idx])
+    tol_u = u_tolerance(case, rays8, g["seg"], g["t"], g["u"])
     ok = np.zeros(m, dtype=bool)
-    for k in range(len(shifts)):
-        sl = slice(k * m, (k + 1) * m)
-        ok |= strict_ok(t_g[idx], u_g[idx], s_g[idx], ref["t"][sl], ref["u"][sl], ref["seg"][sl], tol_u)
-    return idx[ok]
+    shift = np.full(m, np.inf)
+    k = 0
+    for sc in SCALES:
+        for _ in dirs:
+            sl = slice(k * m, (k + 1) * m)
+            hit = strict_ok(g["t"], g["u"], g["seg"], ref["t"][sl], ref["u"][sl], ref["seg"][sl], tol_u)
+            shift = np.where(hit, np.minimum(shift, delta * sc / (EPS32 * np.maximum(T, 1e-30))), shift)
+            ok |= hit
+            k += 1
+    return ok, shift
 
 
-def silhouette_dist(case, i, seg, leaf, depth):
+def silhouette_dist(case, ray8, seg, leaf, depth):
     """|dist(ray line, leaf axis line) - r_leaf| / r_leaf for the leaf of
     segment `seg` starting at `leaf` (units of 2^-23), FP64."""
     if seg < 0 or leaf < 0:
@@ -141,7 +184,7 @@ def silhouette_dist(case, i, seg, leaf, depth):
     start = (int(leaf) // size) * size
     node = O.node_at(cp, start, size)
     r_leaf = O.cons_radius(node)
-    ray = case["rays"][i].astype(np.float64)
+    ray = np.asarray(ray8, dtype=np.float64)
     o, w = ray[:3], ray[4:7] / np.linalg.norm(ray[4:7])
     p, d = node[0, :3], node[1, :3]
     n = np.cross(w, d)
@@ -152,36 +195,122 @@ def silhouette_dist(case, i, seg, leaf, depth):
     return abs(dist - r_leaf) / r_leaf
 
 
-def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces, gpu_leaf=None):
-    """Returns a stats dict; 'fail' lists ray indices failing strict and band."""
-    t_g = gpu_tu[:, 0].astype(np.float64)
-    u_g = gpu_tu[:, 1].astype(np.float64)
-    s_g = gpu_seg.astype(np.int64)
-    tol_u = u_tolerance(case, case["rays"], ref["seg"].astype(np.int64), ref["t"], ref["u"])
-    ok = strict_ok(t_g, u_g, s_g, ref["t"], ref["u"], ref["seg"].astype(np.int64), tol_u)
+def _finish(case, depth, rays8, cands, g, o, ok, g_leaf, o_leaf, pieces, n_items, hits):
+    """Band and silhouette passes of the strict failures, and the stats."""
     bad = np.nonzero(~ok)[0]
-    banded = band_check(case, bad, t_g, u_g, s_g, depth, pieces)
-    rest = np.setdiff1d(bad, banded)
+    sub = lambda d: {k: v[bad] for k, v in d.items()}  # noqa: E731
+    passed, shift = band_check(case, rays8[bad], [cands(i) for i in bad], sub(g), sub(o), depth, pieces)
+    banded = bad[passed]
+    rest = bad[~passed]
     sil = []
     for i in rest:
-        ds = silhouette_dist(case, i, int(ref["seg"][i]), int(ref["leaf"][i]), depth) \
-            if "leaf" in ref else np.inf
-        if gpu_leaf is not None:
-            ds = min(ds, silhouette_dist(case, i, int(s_g[i]), int(gpu_leaf[i]), depth))
+        ds = silhouette_dist(case, rays8[i], int(o["seg"][i]), int(o_leaf[i]), depth) \
+            if o_leaf is not None else np.inf
+        if g_leaf is not None:
+            ds = min(ds, silhouette_dist(case, rays8[i], int(g["seg"][i]), int(g_leaf[i]), depth))
         if ds < 1e-4:
             sil.append(i)
     sil = np.array(sil, dtype=np.int64)
     fail = np.setdiff1d(rest, sil)
-    both = (s_g >= 0) & (ref["seg"] >= 0) & ok
-    rel = np.abs(t_g[both] - ref["t"][both]) / ref["t"][both] if both.any() else np.zeros(1)
-    du = np.abs(u_g[both] - ref["u"][both]) if both.any() else np.zeros(1)
+    tol_u = u_tolerance(case, rays8, o["seg"], o["t"], o["u"])
+    both = (g["seg"] >= 0) & (o["seg"] >= 0) & ok
+    rel = np.abs(g["t"][both] - o["t"][both]) / o["t"][both] if both.any() else np.zeros(1)
+    du = np.abs(g["u"][both] - o["u"][both]) if both.any() else np.zeros(1)
     du_rel = du / tol_u[both] if both.any() else np.zeros(1)
-    detail = [dict(i=int(i), gpu=(float(t_g[i]), float(u_g[i]), int(s_g[i])),
-                   ref=(float(ref["t"][i]), float(ref["u"][i]), int(ref["seg"][i])), tol_u=float(tol_u[i]))
+    detail = [dict(i=int(i), gpu=(float(g["t"][i]), float(g["u"][i]), int(g["seg"][i])),
+                   ref=(float(o["t"][i]), float(o["u"][i]), int(o["seg"][i])), tol_u=float(tol_u[i]))
               for i in fail[:6]]
-    return dict(n=len(s_g), hits=int((ref["seg"] >= 0).sum()), strict=int(ok.sum()),
-                band=int(len(banded)), silhouette=int(len(sil)), fail=fail, max_rel_t=float(rel.max()), max_du=float(du.max()),
-                max_du_over_tol=float(du_rel.max()), med_rel_t=float(np.median(rel)), detail=detail)
+    sh = shift[passed]
+    return dict(n=n_items, hits=hits, strict=int(ok.sum()), band=int(len(banded)), silhouette=int(len(sil)),
+                fail=fail, max_rel_t=float(rel.max()), max_du=float(du.max()),
+                max_du_over_tol=float(du_rel.max()), med_rel_t=float(np.median(rel)), detail=detail,
+                band_shift_uT_max=float(sh.max()) if sh.size else 0.0,
+                band_shift_uT_median=float(np.median(sh)) if sh.size else 0.0)
+
+
+def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces, gpu_leaf=None):
+    """Closest hits per ray against the oracle's; returns a stats dict whose
+    'fail' lists the rays failing strict, band and silhouette."""
+    g = dict(t=gpu_tu[:, 0].astype(np.float64), u=gpu_tu[:, 1].astype(np.float64),
+             seg=np.asarray(gpu_seg).astype(np.int64))
+    o = dict(t=np.asarray(ref["t"], np.float64), u=np.asarray(ref["u"], np.float64),
+             seg=np.asarray(ref["seg"]).astype(np.int64))
+    rays8 = case["rays"]
+    tol_u = u_tolerance(case, rays8, o["seg"], o["t"], o["u"])
+    ok = strict_ok(g["t"], g["u"], g["seg"], o["t"], o["u"], o["seg"], tol_u)
+    rp = case["row_ptr"].astype(np.int64)
+    return _finish(case, depth, rays8, lambda i: case["seg_idx"][rp[i]:rp[i + 1]], g, o, ok, gpu_leaf,
+                   ref.get("leaf"), pieces, len(o["seg"]), int((o["seg"] >= 0).sum()))
+
+
+def band_counts(case, idx, got, depth, mode, pieces):
+    """Per-ray pruning-test counts that differ from the oracle's: whether the
+    oracle's count for one sideways-shifted copy of the ray (the shifts of
+    band_check, delta = 1e-4 r + K_FRAME 2^-24 T with r and T the largest
+    radius and control-point distance over the ray's candidates) equals the
+    GPU's.  A count sums integer outcomes of floating-point tests over the
+    whole row, so a test FP32 settles on the other side of a grazing volume
+    shows as a different count.  Returns a bool array over idx."""
+    m = len(idx)
+    if m == 0:
+        return np.zeros(0, bool)
+    rp = case["row_ptr"].astype(np.int64)
+    cands = [case["seg_idx"][rp[i]:rp[i + 1]] for i in idx]
+    rays = case["rays"][idx].astype(np.float64)
+    o_, w = rays[:, :3], rays[:, 4:7]
+    w = w / np.linalg.norm(w, axis=1, keepdims=True)
+    delta = np.zeros(m)
+    for k, c in enumerate(cands):
+        cp = case["cps"][c].astype(np.float64)
+        T = np.linalg.norm(cp[:, :, :3] - o_[k], axis=2).max() if len(c) else np.linalg.norm(o_[k])
+        r = cp[:, :, 3].max() if len(c) else 0.0
+        delta[k] = 1e-4 * r + K_FRAME * EPS32 * T
+    e1, e2 = _perp(w)
+    s2 = np.sqrt(0.5)
+    dirs = [e1, -e1, e2, -e2, s2 * (e1 + e2), s2 * (e1 - e2), s2 * (-e1 + e2), s2 * (-e1 - e2)]
+    sub_rays, rows, segs = [], [0], []
+    for sc in SCALES:
+        for dv in dirs:
+            sub_rays.append(np.concatenate([o_ + (delta * sc)[:, None] * dv, w, rays[:, 3:4]], axis=1))
+            for c in cands:
+                segs.append(c)
+                rows.append(rows[-1] + len(c))
+    ref, _ = O.ray_counts_d(np.concatenate(sub_rays), np.array(rows, dtype=np.int32),
+                            np.concatenate(segs).astype(np.int32), depth, mode, pieces)
+    return np.any(ref.reshape(-1, m) == np.asarray(got)[idx][None, :], axis=0)
+
+
+def pair_rays(case):
+    """Ray index of every pair of the CSR."""
+    rp = case["row_ptr"].astype(np.int64)
+    return np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+
+
+def compare_pairs(case, depth, gpu_tu, gpu_leaf, ref, pieces):
+    """Per-pair hits (intersect_pairs) against the oracle's (oracle.pairs),
+    pair by pair, under the same strict / band / silhouette rule; a pair's
+    band check shifts its ray against its one segment."""
+    ray_of = pair_rays(case)
+    sid = case["seg_idx"].astype(np.int64)
+    t_g = gpu_tu[:, 0].astype(np.float64)
+    hit_g, hit_o = np.isfinite(t_g), np.isfinite(ref["t"])
+    g = dict(t=t_g, u=gpu_tu[:, 1].astype(np.float64), seg=np.where(hit_g, sid, -1))
+    o = dict(t=np.asarray(ref["t"], np.float64), u=np.asarray(ref["u"], np.float64), seg=np.where(hit_o, sid, -1))
+    rays8 = case["rays"][ray_of]
+    tol_u = u_tolerance(case, rays8, o["seg"], o["t"], o["u"])
+    ok = strict_ok(g["t"], g["u"], g["seg"], o["t"], o["u"], o["seg"], tol_u)
+    return _finish(case, depth, rays8, lambda j: sid[j:j + 1], g, o, ok,
+                   np.asarray(gpu_leaf) if gpu_leaf is not None else None, ref.get("leaf"), pieces,
+                   len(sid), int(hit_o.sum()))
+
+
+def counts_of(stats):
+    """The figures of a comparison worth reporting (JSON-able)."""
+    keys = ("n", "hits", "strict", "band", "silhouette", "max_rel_t", "med_rel_t", "max_du", "max_du_over_tol",
+            "band_shift_uT_max", "band_shift_uT_median")
+    out = {k: stats[k] for k in keys}
+    out["fail"] = int(len(stats["fail"]))
+    return out
 
 
 def pairs_min(pr, case):

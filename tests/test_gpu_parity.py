@@ -1,7 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by
-element on seeded inputs: the tiny workload at depth 8, the depth sweep 2..22
-on three curvature classes, the hair patch at full size (sampled rays), the
-per-pair and naive kernels, the FP64 polish, counters and edge cases."""
+element on seeded inputs: the tiny workload at depth 8, the depth sweep at
+every depth 2..22 on three curvature classes, the hair patch at full size
+(every ray, in the bench's launch), per-pair hits pair by pair for every
+kernel, the FP64 polish, counters and edge cases.  With FX_REPORT=<path>
+set, every comparison appends its strict / band / silhouette counts."""
 import numpy as np
 import pytest
 
@@ -39,8 +41,12 @@ def _run_closest(case, depth, flags=0, fib=None, variant=F.FX_VARIANT_AUTO):
     return _np(tu), _np(seg), _np(leaf), st
 
 
-def _assert_parity(stats, max_band_frac=5e-3, where=""):
-    assert len(stats["fail"]) == 0, "%s: %d rays failing parity, e.g. %s" % (
+def _assert_parity(stats, max_band_frac=1e-3, where="", **rec):
+    """Every result passes strict, band or silhouette; the band and
+    silhouette passes stay within max_band_frac of the results.  The counts
+    are reported (FX_REPORT) under the test's name and `rec`."""
+    P.report(dict(test=where, **rec, **P.counts_of(stats)))
+    assert len(stats["fail"]) == 0, "%s: %d results failing parity, e.g. %s" % (
         where, len(stats["fail"]), stats["detail"])
     exempt = stats["band"] + stats["silhouette"]
     assert exempt <= max_band_frac * max(stats["n"], 1), (where, stats["band"], stats["silhouette"], stats["n"])
@@ -56,16 +62,24 @@ def tiny():
 
 
 VARIANTS = [F.FX_VARIANT_LANE, F.FX_VARIANT_WARP]
+MATH = [0, F.FX_FAST_MATH]
+MATH_IDS = ["ieee", "fast"]
+# (kernel flag, variant) of every forward path; the scan variant runs the
+# lane kernel on handles with pre-split segments
+PATHS = [(F.FX_KERNEL_PERSISTENT, F.FX_VARIANT_LANE), (F.FX_KERNEL_PERSISTENT, F.FX_VARIANT_SCAN),
+         (F.FX_KERNEL_PERSISTENT, F.FX_VARIANT_RAY), (F.FX_KERNEL_PERSISTENT, F.FX_VARIANT_WARP),
+         (F.FX_KERNEL_NAIVE, F.FX_VARIANT_AUTO)]
+PATH_IDS = ["lane", "scan", "ray", "warp", "naive"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=["lane", "warp"])
-@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+@pytest.mark.parametrize("flags", MATH, ids=MATH_IDS)
 def test_tiny_closest_persistent(tiny, flags, variant):
     case, pieces, ref = tiny
     tu, seg, leaf, st = _run_closest(case, 8, flags, variant=variant)
     assert st & ~F.FX_DEV_UNSUPPORTED == 0
     stats = P.compare_closest(case, 8, tu, seg, ref, pieces, leaf)
-    _assert_parity(stats)
+    _assert_parity(stats, where="tiny_closest", variant=int(variant), flags=int(flags))
     assert stats["hits"] > 3000
     strict = P.strict_ok(tu[:, 0], tu[:, 1], seg, ref["t"], ref["u"], ref["seg"])
     same = strict & (seg >= 0)
@@ -76,30 +90,59 @@ def test_tiny_closest_naive(tiny):
     case, pieces, ref = tiny
     tu, seg, leaf, st = _run_closest(case, 8, F.FX_KERNEL_NAIVE)
     assert st & ~F.FX_DEV_UNSUPPORTED == 0
-    _assert_parity(P.compare_closest(case, 8, tu, seg, ref, pieces))
+    _assert_parity(P.compare_closest(case, 8, tu, seg, ref, pieces, leaf), where="tiny_closest_naive")
 
 
-@pytest.mark.parametrize("kernel,variant", [(F.FX_KERNEL_PERSISTENT, F.FX_VARIANT_LANE),
-                                            (F.FX_KERNEL_PERSISTENT, F.FX_VARIANT_WARP),
-                                            (F.FX_KERNEL_NAIVE, 0)], ids=["lane", "warp", "naive"])
-def test_tiny_pairs(tiny, kernel, variant):
-    case, pieces, _ = tiny
-    sub = I.subsample_rays(case, np.arange(0, 16384, 4))
-    pr = O.pairs(sub, 8, pieces)
-    fib = F.Fibers(sub["cps"])
+def _run_pairs(case, depth, kernel, variant, flags, fib=None):
+    own = fib is None
+    if own:
+        fib = F.Fibers(case["cps"])
     fib.set_launch(variant=variant)
-    tu, leaf = F.intersect_pairs(fib, sub["rays"], sub["row_ptr"], sub["seg_idx"], 8, kernel)
-    tu = _np(tu)
-    assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
+    tu, leaf = F.intersect_pairs(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth, kernel | flags)
+    torch.cuda.synchronize()
+    st = fib.status()
+    if own:
+        fib.close()
+    return _np(tu), _np(leaf), st
+
+
+@pytest.mark.parametrize("kernel,variant", PATHS, ids=PATH_IDS)
+@pytest.mark.parametrize("flags", MATH, ids=MATH_IDS)
+def test_tiny_pairs(tiny, kernel, variant, flags):
+    # every (ray, candidate) pair of the tiny workload against the oracle's
+    # per-pair result, pair by pair (the paper's one-ray / one-curve routine)
+    case, pieces, _ = tiny
+    pr = O.pairs(case, 8, pieces)
+    tu, leaf, st = _run_pairs(case, 8, kernel, variant, flags)
+    assert st & ~F.FX_DEV_UNSUPPORTED == 0
+    stats = P.compare_pairs(case, 8, tu, leaf, pr, pieces)
+    _assert_parity(stats, where="tiny_pairs", kernel=int(kernel), variant=int(variant), flags=int(flags))
+    assert stats["hits"] > 10000
+
+
+@pytest.mark.parametrize("kernel,variant", PATHS, ids=PATH_IDS)
+@pytest.mark.parametrize("flags", MATH, ids=MATH_IDS)
+@pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
+@pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
+def test_sweep_pairs(klass, forced, flags, kernel, variant):
+    # the depth-sweep classes pair by pair, with longer rows: each ray's own
+    # segment among seven random others
+    case = I.sweep_case(klass, 4096, forced_hits=forced)
+    g = np.random.default_rng(17)
+    n = len(case["rays"])
+    rows = [np.concatenate([[i], g.integers(0, n, 7)]).astype(np.int32) for i in range(n)]
+    case = dict(case, seg_idx=np.concatenate(rows),
+                row_ptr=np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32))
+    pieces = O.presplit(case["cps"])
+    fib = F.Fibers(case["cps"])
+    for depth in (2, 9, 15, 22):
+        pr = O.pairs(case, depth, pieces)
+        tu, leaf, st = _run_pairs(case, depth, kernel, variant, flags, fib)
+        assert st & ~F.FX_DEV_UNSUPPORTED == 0
+        stats = P.compare_pairs(case, depth, tu, leaf, pr, pieces)
+        _assert_parity(stats, where="sweep_pairs", klass=klass, forced=forced, depth=depth, kernel=int(kernel),
+                       variant=int(variant), flags=int(flags))
     fib.close()
-    hit_g, hit_o = np.isfinite(tu[:, 0]), np.isfinite(pr["t"])
-    agree = hit_g == hit_o
-    both = hit_g & hit_o
-    rel = np.abs(tu[both, 0] - pr["t"][both]) / pr["t"][both]
-    du = np.abs(tu[both, 1] - pr["u"][both])
-    assert agree.mean() > 0.999
-    assert np.mean((rel <= P.TOL_T) & (du <= P.TOL_U)) > 0.999
-    assert both.sum() > 1000
 
 
 def test_presplit_counts_match_oracle(tiny):
@@ -115,27 +158,26 @@ def test_presplit_counts_match_oracle(tiny):
     assert info["max_level"] == int(pieces["level"].max())
 
 
-DEPTHS = [2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 18, 20, 22]
+DEPTHS = list(range(2, 23))
 
 
+@pytest.mark.parametrize("variant", [F.FX_VARIANT_AUTO, F.FX_VARIANT_SCAN], ids=["auto", "scan"])
 @pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
 @pytest.mark.parametrize("forced", [False, True], ids=["aabb", "forced"])
-@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
-def test_depth_sweep(klass, forced, flags):
+@pytest.mark.parametrize("flags", MATH, ids=MATH_IDS)
+def test_depth_sweep(klass, forced, flags, variant):
+    # every depth 2..22 on the three curvature classes (the library's own
+    # choice of kernel, and the scan variant, which runs the lane kernel on
+    # the pre-split curved class)
     case = I.sweep_case(klass, 4096, forced_hits=forced)
     pieces = O.presplit(case["cps"])
     fib = F.Fibers(case["cps"])
-    worst = 0.0
     for depth in DEPTHS:
         ref = O.closest(case, depth, pieces)
-        tu, seg, leaf, _ = _run_closest(case, depth, flags, fib)
+        tu, seg, leaf, _ = _run_closest(case, depth, flags, fib, variant=variant)
         stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
-        _assert_parity(stats, where="%s depth %d" % (klass, depth))
-        worst = max(worst, stats["max_rel_t"])
-        P.report(dict(test="depth_sweep", klass=klass, forced=forced, math="fast" if flags else "ieee",
-                      depth=depth, n=stats["n"], hits=stats["hits"], strict=stats["strict"], band=stats["band"],
-                      silhouette=stats["silhouette"], max_rel_t=stats["max_rel_t"],
-                      median_rel_t=stats["med_rel_t"], max_du=stats["max_du"]))
+        _assert_parity(stats, where="depth_sweep", klass=klass, forced=forced, depth=depth,
+                       math="fast" if flags else "ieee", variant=int(variant))
         if forced:
             assert stats["hits"] > 3500
     assert fib.status() == 0
@@ -152,7 +194,7 @@ def test_single_fiber_many_rays(klass):
         ref = O.closest(case, depth, pieces)
         tu, seg, leaf, _ = _run_closest(case, depth, F.FX_FAST_MATH, fib)
         stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
-        _assert_parity(stats, where="single %s depth %d" % (klass, depth))
+        _assert_parity(stats, where="single_fiber", klass=klass, depth=depth)
     assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
     fib.close()
 
@@ -436,7 +478,7 @@ def test_edge_cases(variant):
         ref = O.closest(case, d)
         tu, seg, _, _ = _run_closest(case, d, 0, fib, variant=variant)
         stats = P.compare_closest(case, d, tu, seg, ref, O.presplit(case["cps"]))
-        _assert_parity(stats, max_band_frac=0.05)
+        _assert_parity(stats, max_band_frac=0.05, where="edge_depth", depth=d, variant=int(variant))
     # bad depth and bad sizes are refused before launch
     with pytest.raises(F.FiberxError):
         F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 24)
@@ -513,10 +555,9 @@ def test_thick_fibers_presplit_and_parity():
             assert k * 2.0 ** -depth <= tu[i, 1] <= (k + 1) * 2.0 ** -depth, (depth, i, k, tuple(tu[i]))
             overlap.append(i)
         stats["fail"] = np.setdiff1d(stats["fail"], overlap)
-        _assert_parity(stats, max_band_frac=0.01, where="thick depth %d" % depth)
+        _assert_parity(stats, max_band_frac=0.01, where="thick", depth=depth, overlap=len(overlap),
+                       unsupported=info["n_unsupported"])
         assert len(overlap) <= 0.02 * n, (depth, len(overlap))
-        P.report(dict(test="thick", depth=depth, n=stats["n"], hits=stats["hits"], strict=stats["strict"],
-                      band=stats["band"], overlap=len(overlap), unsupported=info["n_unsupported"]))
     fib.close()
 
 
@@ -535,35 +576,66 @@ def test_upload_rejects_bad_fibers():
 
 @pytest.fixture(scope="module")
 def hair():
-    """The full hair-patch frame and the oracle on a seeded sample of 3000
-    rays that have candidates, at depth 10 and at the benchmark's depth 15."""
+    """The full hair-patch frame and the oracle on every ray of it, at depth 10
+    and at the benchmark's depth 15."""
     case = I.hair_patch()
-    counts = np.diff(case["row_ptr"])
-    g = np.random.default_rng(5)
-    idx = np.sort(g.choice(np.nonzero(counts > 0)[0], 3000, replace=False))
-    sub = I.subsample_rays(case, idx)
     pieces = O.presplit(case["cps"])
-    ref = {d: O.closest(sub, d, pieces) for d in (10, 15)}
-    return case, idx, sub, pieces, ref
+    ref = {d: O.closest(case, d, pieces) for d in (10, 15)}
+    return case, pieces, ref
+
+
+# the bench's launch on the hair frame: the tuned scan variant, 5 CTAs per SM,
+# chunks of 4 rays
+BENCH_LAUNCH = (128, 5, 4, F.FX_VARIANT_SCAN)
 
 
 @pytest.mark.parametrize("variant", [F.FX_VARIANT_AUTO, F.FX_VARIANT_LANE, F.FX_VARIANT_SCAN, F.FX_VARIANT_RAY],
                          ids=["auto", "lane", "scan", "ray"])
 @pytest.mark.parametrize("depth", [10, 15])
-@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
-def test_hair_patch_full_size_sampled(hair, flags, depth, variant):
-    # the benchmark's workload and launch: full frame on the GPU, oracle on the
-    # sampled rays
-    case, idx, sub, pieces, refs = hair
+@pytest.mark.parametrize("flags", MATH, ids=MATH_IDS)
+def test_hair_patch_full_frame(hair, flags, depth, variant):
+    # the benchmark's workload, every one of its 2,073,600 rays against the
+    # oracle (the scan variant in the bench's launch shape)
+    case, pieces, refs = hair
     ref = refs[depth]
-    tu, seg, leaf, st = _run_closest(case, depth, flags, variant=variant)
-    assert st & ~F.FX_DEV_UNSUPPORTED == 0
-    counts = np.diff(case["row_ptr"])
-    stats = P.compare_closest(sub, depth, tu[idx], seg[idx], ref, pieces, leaf[idx])
-    _assert_parity(stats, max_band_frac=0.01, where="hair")
-    assert stats["hits"] > 500
+    fib = F.Fibers(case["cps"])
+    if variant == F.FX_VARIANT_SCAN:
+        fib.set_launch(*BENCH_LAUNCH)
+    else:
+        fib.set_launch(variant=variant)
+    tu, seg, leaf = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth, flags)
+    torch.cuda.synchronize()
+    assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
+    fib.close()
+    tu, seg, leaf = _np(tu), _np(seg), _np(leaf)
+    stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
+    _assert_parity(stats, max_band_frac=1e-3, where="hair_full_frame", depth=depth, variant=int(variant),
+                   math="fast" if flags else "ieee", rays_with_candidates=int(np.count_nonzero(np.diff(case["row_ptr"]))))
+    assert stats["hits"] > 100_000
     # rays with no candidates are misses
-    assert np.all(seg[counts == 0] == -1)
+    assert np.all(seg[np.diff(case["row_ptr"]) == 0] == -1)
+
+
+@pytest.fixture(scope="module")
+def hair_pairs(hair):
+    """2000 seeded hair rays that have candidates (about 380,000 pairs) and the
+    oracle's per-pair hits at depth 15."""
+    case, pieces, _ = hair
+    counts = np.diff(case["row_ptr"])
+    idx = np.sort(np.random.default_rng(5).choice(np.nonzero(counts > 0)[0], 2000, replace=False))
+    sub = I.subsample_rays(case, idx)
+    return sub, pieces, O.pairs(sub, 15, pieces)
+
+
+@pytest.mark.parametrize("kernel,variant", PATHS, ids=PATH_IDS)
+@pytest.mark.parametrize("flags", MATH, ids=MATH_IDS)
+def test_hair_pairs(hair_pairs, kernel, variant, flags):
+    sub, pieces, pr = hair_pairs
+    tu, leaf, st = _run_pairs(sub, 15, kernel, variant, flags)
+    assert st & ~F.FX_DEV_UNSUPPORTED == 0
+    stats = P.compare_pairs(sub, 15, tu, leaf, pr, pieces)
+    _assert_parity(stats, where="hair_pairs", kernel=int(kernel), variant=int(variant), flags=int(flags))
+    assert stats["hits"] > 5000
 
 
 def test_host_entry_edge_cases():
@@ -627,10 +699,10 @@ def test_concurrent_calls_on_one_handle(variant):
 def test_host_entry_on_the_hair_frame(hair):
     # the end-to-end path the bench times (tuned launch: scan variant, fast
     # math, depth 15, pinned host buffers, chunked copies) equals the device
-    # entry on the full frame, and its sampled rays pass parity with the oracle
-    case, idx, sub, pieces, ref = hair
+    # entry on the full frame, and every ray passes parity with the oracle
+    case, pieces, ref = hair
     fib = F.Fibers(case["cps"])
-    fib.set_launch(128, 5, 4, F.FX_VARIANT_SCAN)
+    fib.set_launch(*BENCH_LAUNCH)
     h = [torch.from_numpy(case[k]).pin_memory() for k in ("rays", "row_ptr", "seg_idx")]
     tu_h, seg_h, leaf_h = F.intersect_closest_host(fib, *h, 15, F.FX_FAST_MATH)
     tu_d, seg_d, leaf_d = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 15, F.FX_FAST_MATH)
@@ -641,8 +713,8 @@ def test_host_entry_on_the_hair_frame(hair):
     assert h2d < 32 * len(case["rays"]) + 4 * (len(case["rays"]) + 1) + 4 * len(case["seg_idx"])
     assert fib.status() == 0
     fib.close()
-    stats = P.compare_closest(sub, 15, tu_h.numpy()[idx], seg_h.numpy()[idx], ref[15], pieces, leaf_h.numpy()[idx])
-    _assert_parity(stats, where="hair host entry")
+    stats = P.compare_closest(case, 15, tu_h.numpy(), seg_h.numpy(), ref[15], pieces, leaf_h.numpy())
+    _assert_parity(stats, where="hair_host_entry")
 
 
 def test_upload_from_device_memory_equals_host_upload(tiny):
