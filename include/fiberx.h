@@ -25,6 +25,9 @@
  *    available from fx_last_error().
  *  - Device-side conditions never trap: they set bits of the handle's sticky
  *    status word (FX_DEV_*), read and cleared by fx_stream_status.
+ *  - A handle's arrays live on the device that was current at its upload;
+ *    every intersect_* call must be made with that device current
+ *    (FX_EDEVICE otherwise, before any launch).
  *  - Calls on one handle may run concurrently on unordered streams: each
  *    call's work-queue counter and scratch come from the handle's
  *    stream-ordered memory pool.  They share the sticky status word and the
@@ -51,7 +54,7 @@ typedef enum {
     FX_EUNSUPPORTED = -4, /* option not supported */
     FX_ETIMEOUT = -5,     /* reserved: a bounded device wait ran out */
     FX_EDEPTH = -6,       /* subdivision depth outside [0, 23] */
-    FX_EDEVICE = -7       /* no usable sm_103 device */
+    FX_EDEVICE = -7       /* no usable sm_103 device, or the current device is not the handle's */
 } fx_status;
 
 /* Sticky device status bits (fx_stream_status). */
@@ -153,11 +156,10 @@ fx_status fiber_upload(const float *cps, int64_t n_seg, int32_t cps_on_device,
  * q3 = p2) and then uploaded as fiber_upload does, so every intersect_* call
  * and its u, leaf and segment ids refer to the quadratic segment.  A
  * quadratic that meets App. B.1's constraint raises to a cubic that meets the
- * five cubic constraints of Sec. 3.4, so it is not pre-split.  The handle's
- * control points for intersect_backward are the raised cubic's: grad_cps is
- * n_seg x 4 x 4, with respect to q0..q3 (the chain rule to p0..p2 is
- * dq0/dp0 = 1, dq1/dp0 = 1/3, dq1/dp1 = 2/3, dq2/dp1 = 2/3, dq2/dp2 = 1/3,
- * dq3/dp2 = 1).  Errors as fiber_upload.
+ * five cubic constraints of Sec. 3.4, so it is not pre-split.
+ * intersect_backward on such a handle returns the gradient with respect to
+ * the quadratic control points p0..p2 (n_seg x 3 x 4; the kernel applies the
+ * chain rule through the elevation).  Errors as fiber_upload.
  */
 fx_status fiber_upload_quadratic(const float *cps, int64_t n_seg, int32_t cps_on_device,
                                  const fx_upload_opts *opts, void *stream, fx_fibers **out);
@@ -231,8 +233,12 @@ fx_status intersect_pairs(const fx_fibers *f, const float *rays, int64_t n_ray,
  * theorem).  End-disk hits (u = 0 or 1) use G1 with u fixed.
  *
  * Inputs: rays (as above), tu and seg from intersect_closest, grad_t (n_ray
- * floats, dL/dt_i).  Output: grad_cps (n_seg x 16 floats, same layout as
- * cps), ACCUMULATED (+=) with atomics; zero it first for a fresh gradient.
+ * floats, dL/dt_i).  Output: grad_cps, same layout as the cps the handle was
+ * uploaded from -- n_seg x 16 floats for fiber_upload, n_seg x 12 for
+ * fiber_upload_quadratic (with respect to p0..p2: the adjoint of the raised
+ * cubic q0..q3 carried back through q0 = p0, q1 = (p0 + 2 p1) / 3,
+ * q2 = (2 p1 + p2) / 3, q3 = p2) -- ACCUMULATED (+=) with atomics; zero it
+ * first for a fresh gradient.
  * Misses and rays with grad_t == 0 contribute nothing; hits whose system
  * is singular (|det J| tiny: grazing) are skipped and counted in
  * *n_skipped_dev (device int64, nullable).
@@ -275,10 +281,11 @@ fx_status intersect_normals(const fx_fibers *f, const float *rays, int64_t n_ray
  *     a hit node are tested (two counts), the one with the smaller z_min is
  *     searched first and the other tested again (one count) when taken up;
  *     the search does not end at the first leaf hit.
+ * A pre-split segment's pieces are searched in order, each to depth - level
+ * (the unsplit curve's leaves), with the closest hit so far as t_max.
  * Output: counts, n_ray uint32 (saturating).  flags: FX_FAST_MATH,
- * FX_CHECK_INDEX, FX_COUNT_BOXES.  Handles whose segments are single level-0
- * pieces only (FX_EUNSUPPORTED otherwise).  Errors: FX_EINVAL, FX_EDEPTH,
- * FX_EUNSUPPORTED, FX_ECUDA.
+ * FX_CHECK_INDEX, FX_COUNT_BOXES.  Errors: FX_EINVAL, FX_EDEPTH, FX_EDEVICE,
+ * FX_ECUDA.
  */
 fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray, const int32_t *row_ptr,
                            const int32_t *seg_idx, int64_t n_pair, int32_t depth, uint32_t flags,
@@ -351,9 +358,13 @@ fx_status fx_stream_status(fx_fibers *f, void *stream, uint32_t *device_flags);
  * FX_COUNT, FX_CHECK_INDEX; FX_POLISH_FP64 needs a non-null leaf).
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array: each clears the
- * keys it uses before its kernels run, and calls that overlap on the GPU
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process; make that first call before any stream capture.  A
+ * cudaDeviceReset destroys the array with every other allocation of the
+ * device (and every handle): the kept address is then stale, so do not use
+ * the library on a device after resetting it.  The handle's device must be
+ * current (FX_EDEVICE otherwise).  Every call shares the array: each clears
+ * the keys it uses before its kernels run, and calls that overlap on the GPU
  * (unordered streams) race on it.
  */
 #define FX_NOALLOC_MAX_RAYS (1 << 20)

@@ -40,6 +40,7 @@ unsigned long long* counters_of(const fx_fibers* f) {
 fx_status check_common(const fx_fibers* f, const float* rays, int64_t n_ray, const int32_t* row_ptr,
                        const int32_t* seg_idx, int64_t n_pair, int32_t depth) {
   if (!f) return fail(FX_EINVAL, "null fiber handle");
+  if (!fx::on_handle_device(f)) return fail(FX_EDEVICE, "the current device is not the handle's device");
   if (n_ray < 0 || n_pair < 0) return fail(FX_EINVAL, "negative size");
   if (n_ray > 0x7fffffffLL || n_pair > 0x7fffffffLL)
     return fail(FX_EINVAL, "more than 2^31 - 1 rays or pairs");
@@ -355,7 +356,9 @@ fx_status fiber_upload_quadratic(const float* cps, int64_t n_seg, int32_t cps_on
     }
     for (int k = 0; k < 16; ++k) cps32[16 * i + k] = (float)c[k];
   }
-  return upload_cubics(cps64, cps32, n_seg, opts, s, out);
+  st = upload_cubics(cps64, cps32, n_seg, opts, s, out);
+  if (st == FX_OK) (*out)->quadratic = true;
+  return st;
 }
 
 
@@ -450,10 +453,11 @@ fx_status intersect_backward(const fx_fibers* f, const float* rays, int64_t n_ra
                              const int32_t* seg, const float* grad_t, float* grad_cps,
                              unsigned long long* n_skipped_dev, void* stream) {
   if (!f) return fail(FX_EINVAL, "null fiber handle");
+  if (!fx::on_handle_device(f)) return fail(FX_EDEVICE, "the current device is not the handle's device");
   if (n_ray < 0 || n_ray > 0x7fffffffLL) return fail(FX_EINVAL, "n_ray out of range");
   if (n_ray == 0) return FX_OK;
   if (!rays || !tu || !seg || !grad_t || !grad_cps) return fail(FX_EINVAL, "null argument");
-  FX_CUDA(fx::launch_backward(f->seg_cp, f->n_seg, reinterpret_cast<const float4*>(rays), n_ray,
+  FX_CUDA(fx::launch_backward(f->seg_cp, f->n_seg, f->quadratic, reinterpret_cast<const float4*>(rays), n_ray,
                               reinterpret_cast<const float2*>(tu), seg, grad_t, grad_cps, n_skipped_dev,
                               (cudaStream_t)stream));
   return FX_OK;
@@ -465,7 +469,6 @@ fx_status intersect_counts(const fx_fibers* f, const float* rays, int64_t n_ray,
   fx_status st = check_common(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
   if (st != FX_OK) return st;
   if (n_ray > 0 && !counts) return fail(FX_EINVAL, "null counts output");
-  if (!f->identity) return fail(FX_EUNSUPPORTED, "counts need segments that are single level-0 pieces");
   fx::TraceArgs a = make_args(f, rays, n_ray, row_ptr, seg_idx, n_pair, depth);
   FX_CUDA(fx::launch_counts(a, counts, (flags & FX_COUNT_BOXES) != 0, flags, (cudaStream_t)stream));
   return FX_OK;
@@ -475,6 +478,7 @@ fx_status intersect_normals(const fx_fibers* f, const float* rays, int64_t n_ray
                             const int32_t* seg, const int32_t* leaf, int32_t depth, const int8_t* ray_depth,
                             uint32_t flags, float* normal, void* stream) {
   if (!f) return fail(FX_EINVAL, "null fiber handle");
+  if (!fx::on_handle_device(f)) return fail(FX_EDEVICE, "the current device is not the handle's device");
   if (n_ray < 0 || n_ray > 0x7fffffffLL) return fail(FX_EINVAL, "n_ray out of range");
   if (depth < 0 || depth > fx::kMaxDepth) return fail(FX_EDEPTH, "depth outside [0, 23]");
   if (n_ray == 0) return FX_OK;

@@ -27,6 +27,7 @@ struct fx_fibers {
   int64_t n_seg = 0, n_piece = 0, n_presplit = 0, n_unsupported = 0;
   int32_t max_level = 0;
   bool identity = true;                 // one level-0 piece per segment, none unsupported
+  bool quadratic = false;               // uploaded as quadratics (stored raised to cubics)
   float4 *piece = nullptr;              // n_piece x {p, d, t0, t1} world space
   int32_t *piece_begin = nullptr;       // n_seg + 1
   int32_t *piece_info = nullptr;        // n_piece: level | off << 4 | unsupported << 31
@@ -50,6 +51,13 @@ struct fx_fibers {
 namespace fx {
 
 constexpr int kMaxDepth = 23;
+
+// Whether the calling thread's current device is the one the handle's arrays
+// live on (its kernels must run there).
+inline bool on_handle_device(const fx_fibers *f) {
+  int d = -1;
+  return cudaGetDevice(&d) == cudaSuccess && d == f->device;
+}
 
 struct TraceArgs {
   const float4 *piece;
@@ -182,8 +190,10 @@ cudaError_t fma_peak(int sm_count, int blocks_per_sm, int iters, float *ms, doub
 void set_last_error(const std::string &msg);
 
 // backward.cu
-cudaError_t launch_backward(const float4 *seg_cp, int64_t n_seg, const float4 *rays, int64_t n_ray,
-                            const float2 *tu, const int32_t *seg, const float *grad_t,
+// quadratic: the handle holds raised quadratics; grad_cps is n_seg x 12
+// (p0..p2), else n_seg x 16
+cudaError_t launch_backward(const float4 *seg_cp, int64_t n_seg, bool quadratic, const float4 *rays,
+                            int64_t n_ray, const float2 *tu, const int32_t *seg, const float *grad_t,
                             float *grad_cps, unsigned long long *n_skipped, cudaStream_t s);
 
 }  // namespace fx

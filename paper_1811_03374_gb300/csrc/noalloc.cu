@@ -58,6 +58,9 @@ extern "C" fx_status intersect_closest_noalloc(const fx_fibers* f, const float* 
                                                int64_t n_pair, int32_t depth, uint32_t flags, float* tu,
                                                int32_t* seg, int32_t* leaf, void* stream) {
   if (!f) return fail(FX_EINVAL, "null fiber handle");
+  // the key array looked up below is the current device's; the handle's
+  // arrays must live on that device too
+  if (!fx::on_handle_device(f)) return fail(FX_EDEVICE, "the current device is not the handle's device");
   if (n_ray < 0 || n_pair < 0) return fail(FX_EINVAL, "negative size");
   if (n_ray > FX_NOALLOC_MAX_RAYS)
     return fail(FX_EINVAL, "intersect_closest_noalloc: n_ray exceeds FX_NOALLOC_MAX_RAYS (1048576)");

@@ -50,7 +50,7 @@ __device__ __forceinline__ bool trace_piece(const TraceArgs& a, int piece, const
     } else if (st.bits == 0u) {
       return false;
     } else {
-      jump_up(st.bits, st.start, st.size);
+      take_pending(st.bits, st.start, st.size);
       recompute(st.R, st.start, st.size, st.c);
       slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
       if (cnt) ++cnt[2];
@@ -127,9 +127,10 @@ __global__ void __launch_bounds__(256) k_naive(const TraceArgs a) {
       if (a.leaf) a.leaf[j] = got ? leaf : -1;
       if (a.pair_flags) a.pair_flags[j] = (uint8_t)flags;
     } else if (got) {
-      // t >= 0, so its bit pattern orders like the value; ties keep the
-      // smaller pair index (the earlier candidate)
-      const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (uint32_t)j;
+      // t >= 0, so its bit pattern orders like the value once a -0 (fmaxf
+      // may return either zero) has lost its sign; ties keep the smaller
+      // pair index (the earlier candidate)
+      const unsigned long long key = ((unsigned long long)(__float_as_uint(t) & 0x7fffffffu) << 32) | (uint32_t)j;
       atomicMin(a.scratch + r, key);
     }
   }

@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
         // ---- share the closest hit of this step across the warp -----------
         if (!PAIRS && __any_sync(kFull, leaf_hit)) {
-          const unsigned tb = leaf_hit ? __float_as_uint(hit_t) : 0xffffffffu;
+          // hit_t >= 0 (a -0 loses its sign), so the bit patterns order like the values
+          const unsigned tb = leaf_hit ? (__float_as_uint(hit_t) & 0x7fffffffu) : 0xffffffffu;
           const unsigned tmin = __reduce_min_sync(kFull, tb);
           const unsigned pb = (leaf_hit && tb == tmin) ? (unsigned)my_pos : 0xffffffffu;
           const unsigned pmin = __reduce_min_sync(kFull, pb);

@@ -1,8 +1,11 @@
 """intersect_closest_noalloc (fixed device scratch, no allocation) against
 intersect_closest with the one-thread-per-pair kernel, both called through
 the C ABI on the same inputs, on two calls in a row with different workloads
-so that the second call runs on the keys the first one left behind.  The
-file name keeps it last in collection; it passes alone or after the rest."""
+so that the second call runs on the keys the first one left behind.  Both run
+the same kernels, so their results must be identical bit for bit, with each
+flag the entry accepts (approximate math, the FP64 polish, index checks with
+counters).  The file name keeps it last in collection; it passes alone or
+after the rest."""
 import ctypes
 
 import numpy as np
@@ -10,7 +13,6 @@ import pytest
 
 from paper_1811_03374_gb300 import fiberx as F
 from paper_1811_03374_gb300 import inputs as I
-from tests import _parity as P
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -44,32 +46,52 @@ def _call_noalloc(fib, rays, row_ptr, seg_idx, depth, flags=0, n_ray=None):
     return rc, tu, seg, leaf
 
 
-def _same(case, got, want):
-    tu_g, seg_g = got[1].cpu().numpy(), got[2].cpu().numpy()
-    tu_w, seg_w, _ = (x.cpu().numpy() if x is not None else None for x in want)
-    assert np.array_equal(seg_g, seg_w)
-    hit = seg_w >= 0
-    assert hit.sum() > 0
-    t_g, t_w = tu_g[hit, 0].astype(np.float64), tu_w[hit, 0].astype(np.float64)
-    assert np.all(np.abs(t_g - t_w) <= P.TOL_T * np.abs(t_w))
-    tol_u = P.u_tolerance(case, case["rays"][hit], seg_w[hit], t_w, tu_w[hit, 1].astype(np.float64))
-    assert np.all(np.abs(tu_g[hit, 1].astype(np.float64) - tu_w[hit, 1]) <= tol_u)
-    assert np.all(np.isinf(tu_g[~hit, 0]))
+def _same(got, want):
+    # both run the same one-thread-per-pair kernels on the same inputs: the
+    # results are identical bit for bit
+    for g, w in zip(got[1:], want):
+        np.testing.assert_array_equal(g.cpu().numpy(), w.cpu().numpy())
+    assert (want[1].cpu().numpy() >= 0).sum() > 0
 
 
-@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH])
+FLAGS = [0, F.FX_FAST_MATH, F.FX_POLISH_FP64, F.FX_CHECK_INDEX | F.FX_COUNT]
+
+
+@pytest.mark.parametrize("flags", FLAGS, ids=["ieee", "fast", "polish", "check_count"])
 def test_noalloc_matches_intersect_closest_twice(flags):
     first = I.tiny_case()                          # 16384 rays, dense candidates
     second = I.sweep_case("curved", 4096, forced_hits=True)  # fewer rays: reuses stale keys
     for case in (first, second):
         fib = F.Fibers(case["cps"])
         rays, row_ptr, seg_idx = _dev(case)
+        fib.counters(reset=True)
         want = F.intersect_closest(fib, rays, row_ptr, seg_idx, DEPTH, flags | F.FX_KERNEL_NAIVE)
+        c_want = fib.counters(reset=True)
         got = _call_noalloc(fib, rays, row_ptr, seg_idx, DEPTH, flags)
         torch.cuda.synchronize()
         assert got[0] == F.FX_OK, F.lib().fx_last_error().decode()
-        _same(case, got, want)
+        c_got = fib.counters(reset=True)
+        _same(got, want)
+        if flags & F.FX_COUNT:
+            assert c_got == c_want and c_got["nodes"] > 0
+        assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
         fib.close()
+
+
+def test_noalloc_polish_needs_the_leaf_output():
+    case = I.tiny_case(n_ray=64)
+    fib = F.Fibers(case["cps"])
+    rays, row_ptr, seg_idx = _dev(case)
+    tu = torch.zeros((64, 2), device="cuda")
+    seg = torch.zeros(64, dtype=torch.int32, device="cuda")
+    vp = ctypes.c_void_p
+    rc = F.lib().intersect_closest_noalloc(
+        fib.handle, vp(rays.data_ptr()), 64, vp(row_ptr.data_ptr()), vp(seg_idx.data_ptr()),
+        seg_idx.numel(), DEPTH, F.FX_POLISH_FP64, vp(tu.data_ptr()), vp(seg.data_ptr()), None,
+        vp(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1
+    assert "leaf" in F.lib().fx_last_error().decode()
+    fib.close()
 
 
 def test_noalloc_rejects_more_rays_than_the_array_holds():
