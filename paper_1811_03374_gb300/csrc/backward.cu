@@ -18,6 +18,12 @@
 // hit near an end from the disk in FP32 (u = 1 - 5e-8 rounds to 1), so the
 // classification is geometric.
 // One thread per ray; contributions are added to grad_cps with atomics.
+//
+// Quadratic segments (App. B.1) are stored as their degree elevation,
+// q0 = p0, q1 = (p0 + 2 p1) / 3, q2 = (2 p1 + p2) / 3, q3 = p2 (the same
+// curve), so the adjoint is first formed with respect to q0..q3 and then
+// carried to p0..p2 by the chain rule through that linear map:
+// dL/dp0 = g0 + g1 / 3, dL/dp1 = 2 (g1 + g2) / 3, dL/dp2 = g2 / 3 + g3.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -45,6 +51,7 @@ __device__ __forceinline__ void two_diff(float a, float b, float& hi, float& lo)
   lo = (a - (hi - bb)) - (b + bb);
 }
 
+template <bool QUAD>
 __global__ void __launch_bounds__(256)
     k_backward(const float4* __restrict__ cp, const float4* __restrict__ rays, int64_t n_ray,
                const float2* __restrict__ tu, const int32_t* __restrict__ seg,
@@ -160,29 +167,48 @@ __global__ void __launch_bounds__(256)
   const float v = 1.0f - u;
   const float B[4] = {v * v * v, 3.f * u * v * v, 3.f * u * u * v, u * u * u};
   const float dB[4] = {-3.f * v * v, 3.f * v * v - 6.f * u * v, 6.f * u * v - 3.f * u * u, 3.f * u * u};
-  float* g = grad_cps + 16 * (int64_t)s;
+  // dL/dq_k of the (stored) cubic control points
+  float gq[4][4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const float gx = dB[k] * e.x - B[k] * c1.x, gy = dB[k] * e.y - B[k] * c1.y,
                 gz = dB[k] * e.z - B[k] * c1.z;
     const float hb = -2.f * B[k];
-    atomicAdd(g + 4 * k + 0, -gw * (a1 * gx + a2 * hb * e.x));
-    atomicAdd(g + 4 * k + 1, -gw * (a1 * gy + a2 * hb * e.y));
-    atomicAdd(g + 4 * k + 2, -gw * (a1 * gz + a2 * hb * e.z));
-    atomicAdd(g + 4 * k + 3, -gw * (a2 * hb * c.w));
+    gq[k][0] = -gw * (a1 * gx + a2 * hb * e.x);
+    gq[k][1] = -gw * (a1 * gy + a2 * hb * e.y);
+    gq[k][2] = -gw * (a1 * gz + a2 * hb * e.z);
+    gq[k][3] = -gw * (a2 * hb * c.w);
+  }
+  if (QUAD) {
+    float* g = grad_cps + 12 * (int64_t)s;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      atomicAdd(g + a, fmaf(gq[1][a], 1.f / 3.f, gq[0][a]));
+      atomicAdd(g + 4 + a, (2.f / 3.f) * (gq[1][a] + gq[2][a]));
+      atomicAdd(g + 8 + a, fmaf(gq[2][a], 1.f / 3.f, gq[3][a]));
+    }
+  } else {
+    float* g = grad_cps + 16 * (int64_t)s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) atomicAdd(g + 4 * k + a, gq[k][a]);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_backward(const float4* seg_cp, int64_t n_seg, const float4* rays, int64_t n_ray,
-                            const float2* tu, const int32_t* seg, const float* grad_t, float* grad_cps,
-                            unsigned long long* n_skipped, cudaStream_t s) {
+cudaError_t launch_backward(const float4* seg_cp, int64_t n_seg, bool quadratic, const float4* rays,
+                            int64_t n_ray, const float2* tu, const int32_t* seg, const float* grad_t,
+                            float* grad_cps, unsigned long long* n_skipped, cudaStream_t s) {
   (void)n_seg;
   if (n_ray <= 0) return cudaSuccess;
   const int block = 256;
-  k_backward<<<(unsigned)((n_ray + block - 1) / block), block, 0, s>>>(seg_cp, rays, n_ray, tu, seg, grad_t,
-                                                                       grad_cps, n_skipped);
+  const unsigned grid = (unsigned)((n_ray + block - 1) / block);
+  if (quadratic)
+    k_backward<true><<<grid, block, 0, s>>>(seg_cp, rays, n_ray, tu, seg, grad_t, grad_cps, n_skipped);
+  else
+    k_backward<false><<<grid, block, 0, s>>>(seg_cp, rays, n_ray, tu, seg, grad_t, grad_cps, n_skipped);
   return cudaGetLastError();
 }
 

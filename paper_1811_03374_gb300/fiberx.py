@@ -344,7 +344,8 @@ def intersect_normals(fibers, rays, tu, seg, leaf, depth, flags=0, stream=None, 
 
 def intersect_backward(fibers, rays, tu, seg, grad_t, grad_cps=None, stream=None):
     """dL/d(cps) for L with dL/dt = grad_t; returns (grad_cps [n_seg, 4, 4],
-    number of skipped singular hits as a device tensor)."""
+    or [n_seg, 3, 4] for quadratic fibers, number of skipped singular hits as
+    a device tensor)."""
     import torch
     dev = fibers.device
     rays = _dev(rays, torch.float32, dev)
@@ -352,7 +353,7 @@ def intersect_backward(fibers, rays, tu, seg, grad_t, grad_cps=None, stream=None
     seg = _dev(seg, torch.int32, dev)
     grad_t = _dev(grad_t, torch.float32, dev)
     if grad_cps is None:
-        grad_cps = torch.zeros((fibers.n_seg, 4, 4), dtype=torch.float32, device=dev)
+        grad_cps = torch.zeros((fibers.n_seg, 3 if fibers.quadratic else 4, 4), dtype=torch.float32, device=dev)
     skipped = torch.zeros(1, dtype=torch.int64, device=dev)
     _check(lib().intersect_backward(fibers.handle, _ptr(rays), rays.shape[0], _ptr(tu), _ptr(seg),
                                     _ptr(grad_t), _ptr(grad_cps), _ptr(skipped), _stream(stream)))
@@ -419,11 +420,6 @@ def _autograd():
             if grad_t is None:
                 return (None,) * 7
             g, _ = intersect_backward(ctx.fibers, rays, tu, seg, grad_t.float().contiguous())
-            if ctx.fibers.quadratic:
-                # the adjoint is with respect to the raised cubic q0..q3; the
-                # chain rule through q1 = (p0 + 2 p1) / 3, q2 = (2 p1 + p2) / 3
-                g = torch.stack([g[:, 0] + g[:, 1] / 3.0, (2.0 / 3.0) * (g[:, 1] + g[:, 2]),
-                                 g[:, 2] / 3.0 + g[:, 3]], dim=1)
             return g.reshape(ctx.cps_shape), None, None, None, None, None, None
 
     return FiberIntersect

@@ -1,16 +1,19 @@
 /*
  * c_client.c -- a plain C caller of the fiberx C ABI (no Python, no torch):
- * reads a case from a binary file, uploads the fibers from host memory,
- * copies rays and the candidate CSR to the device with the CUDA runtime,
- * runs intersect_closest (and intersect_pairs with per-pair status bytes),
+ * reads a case from a binary file, uploads the fibers (cubic or quadratic)
+ * from host memory, copies rays and the candidate CSR to the device with the
+ * CUDA runtime, runs intersect_closest (and intersect_pairs with per-pair
+ * status bytes), then intersect_backward for L = the sum of the hit t,
  * copies the results back and writes them to a binary file.
  *
  *   c_client IN OUT DEPTH FLAGS VARIANT
  *
- * IN:  int64 n_seg, n_ray, n_pair; float cps[n_seg * 16]; float rays[n_ray * 8];
+ * IN:  int64 n_seg, n_ray, n_pair, n_cp (4: cubic, 3: quadratic);
+ *      float cps[n_seg * n_cp * 4]; float rays[n_ray * 8];
  *      int32 row_ptr[n_ray + 1]; int32 seg_idx[n_pair]
  * OUT: float tu[n_ray * 2]; int32 seg[n_ray]; int32 leaf[n_ray];
- *      float tu_pairs[n_pair * 2]; uint8 pair_flags[n_pair]; uint32 status
+ *      float tu_pairs[n_pair * 2]; uint8 pair_flags[n_pair]; uint32 status;
+ *      float grad_cps[n_seg * n_cp * 4]
  * Exit status 0 on success; any failing call prints fx_last_error().
  */
 #include <cuda_runtime_api.h>
@@ -64,10 +67,12 @@ int main(int argc, char **argv) {
   const int32_t variant = atoi(argv[5]);
   FILE *in = fopen(argv[1], "rb");
   if (!in) return 2;
-  int64_t n[3];
-  if (fread(n, sizeof(int64_t), 3, in) != 3) return 2;
-  const int64_t n_seg = n[0], n_ray = n[1], n_pair = n[2];
-  float *cps = (float *)read_n(in, (size_t)n_seg * 16 * sizeof(float));
+  int64_t n[4];
+  if (fread(n, sizeof(int64_t), 4, in) != 4) return 2;
+  const int64_t n_seg = n[0], n_ray = n[1], n_pair = n[2], n_cp = n[3];
+  if (n_cp != 3 && n_cp != 4) return 2;
+  const size_t cp_floats = (size_t)n_seg * (size_t)n_cp * 4;
+  float *cps = (float *)read_n(in, cp_floats * sizeof(float));
   float *rays = (float *)read_n(in, (size_t)n_ray * 8 * sizeof(float));
   int32_t *row_ptr = (int32_t *)read_n(in, (size_t)(n_ray + 1) * sizeof(int32_t));
   int32_t *seg_idx = (int32_t *)read_n(in, (size_t)n_pair * sizeof(int32_t));
@@ -76,7 +81,10 @@ int main(int argc, char **argv) {
 
   fx_fibers *fib = NULL;
   fx_upload_opts opts = {8, 1};
-  CHECK_FX(fiber_upload(cps, n_seg, 0, &opts, NULL, &fib));
+  if (n_cp == 4)
+    CHECK_FX(fiber_upload(cps, n_seg, 0, &opts, NULL, &fib));
+  else
+    CHECK_FX(fiber_upload_quadratic(cps, n_seg, 0, &opts, NULL, &fib));
   fx_launch launch;
   CHECK_FX(fx_get_launch(fib, &launch));
   launch.variant = variant;
@@ -99,6 +107,16 @@ int main(int argc, char **argv) {
                              NULL));
   CHECK_FX(intersect_pairs(fib, d_rays, n_ray, d_rp, d_si, n_pair, depth, NULL, flags & ~FX_POLISH_FP64, d_tup,
                            NULL, d_pf, NULL));
+  /* adjoint of L = sum of the hit t: dL/dt = 1 for every ray (misses add nothing) */
+  float *ones = (float *)malloc((size_t)n_ray * sizeof(float) + 1);
+  float *d_gt = NULL, *d_grad = NULL;
+  if (!ones) return 1;
+  for (int64_t i = 0; i < n_ray; ++i) ones[i] = 1.0f;
+  d_gt = (float *)to_device(ones, (size_t)n_ray * sizeof(float));
+  if (!d_gt) return 1;
+  CHECK_CUDA(cudaMalloc((void **)&d_grad, cp_floats * sizeof(float) + 1));
+  CHECK_CUDA(cudaMemset(d_grad, 0, cp_floats * sizeof(float) + 1));
+  CHECK_FX(intersect_backward(fib, d_rays, n_ray, d_tu, d_seg, d_gt, d_grad, NULL, NULL));
   uint32_t status = 0;
   CHECK_FX(fx_stream_status(fib, NULL, &status));
 
@@ -107,12 +125,14 @@ int main(int argc, char **argv) {
   int32_t *leaf = (int32_t *)malloc((size_t)n_ray * sizeof(int32_t) + 1);
   float *tup = (float *)malloc((size_t)n_pair * 2 * sizeof(float) + 1);
   uint8_t *pf = (uint8_t *)malloc((size_t)n_pair + 1);
-  if (!tu || !seg || !leaf || !tup || !pf) return 1;
+  float *grad = (float *)malloc(cp_floats * sizeof(float) + 1);
+  if (!tu || !seg || !leaf || !tup || !pf || !grad) return 1;
   CHECK_CUDA(cudaMemcpy(tu, d_tu, (size_t)n_ray * 2 * sizeof(float), cudaMemcpyDeviceToHost));
   CHECK_CUDA(cudaMemcpy(seg, d_seg, (size_t)n_ray * sizeof(int32_t), cudaMemcpyDeviceToHost));
   CHECK_CUDA(cudaMemcpy(leaf, d_leaf, (size_t)n_ray * sizeof(int32_t), cudaMemcpyDeviceToHost));
   CHECK_CUDA(cudaMemcpy(tup, d_tup, (size_t)n_pair * 2 * sizeof(float), cudaMemcpyDeviceToHost));
   CHECK_CUDA(cudaMemcpy(pf, d_pf, (size_t)n_pair, cudaMemcpyDeviceToHost));
+  CHECK_CUDA(cudaMemcpy(grad, d_grad, cp_floats * sizeof(float), cudaMemcpyDeviceToHost));
 
   FILE *out = fopen(argv[2], "wb");
   if (!out) return 2;
@@ -122,7 +142,12 @@ int main(int argc, char **argv) {
   fwrite(tup, sizeof(float), (size_t)n_pair * 2, out);
   fwrite(pf, 1, (size_t)n_pair, out);
   fwrite(&status, sizeof(status), 1, out);
+  fwrite(grad, sizeof(float), cp_floats, out);
   fclose(out);
+  cudaFree(d_gt);
+  cudaFree(d_grad);
+  free(ones);
+  free(grad);
 
   cudaFree(d_rays);
   cudaFree(d_rp);
