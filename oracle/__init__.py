@@ -69,6 +69,8 @@ def lib():
             L.orc_split_half.argtypes = [vp, vp, vp]; L.orc_split_half.restype = None
             L.orc_ray_counts.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp]
             L.orc_ray_counts.restype = None
+            L.orc_ray_counts_d.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp]
+            L.orc_ray_counts_d.restype = None
             L.orc_presplit_d.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp, i64]
             L.orc_presplit_d.restype = i64
             L.orc_valid_quadratic.argtypes = [vp]; L.orc_valid_quadratic.restype = i32
@@ -222,6 +224,20 @@ def ray_counts(case, depth, mode, pieces=None, nthreads=0):
     t = np.zeros(n)
     lib().orc_ray_counts(_p(rays), n, _p(rp), _p(si), _p(pc), _p(pieces["begin"]), _p(pieces["level"]),
                          int(depth), {"cylinder": 0, "box": 1}[mode], int(nthreads), _p(counts), _p(t))
+    return counts, t
+
+
+def ray_counts_d(rays7, row_ptr, seg_idx, depth, mode, pieces, nthreads=0):
+    """ray_counts() with double-precision rays [n, 7] (o, w, t_max)."""
+    rays7 = np.ascontiguousarray(rays7, dtype=np.float64)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    si = np.ascontiguousarray(seg_idx, dtype=np.int32)
+    pc = np.ascontiguousarray(pieces["cp"], dtype=np.float64).reshape(-1, 16)
+    n = rays7.shape[0]
+    counts = np.zeros(n, np.int64)
+    t = np.zeros(n)
+    lib().orc_ray_counts_d(_p(rays7), n, _p(rp), _p(si), _p(pc), _p(pieces["begin"]), _p(pieces["level"]),
+                           int(depth), {"cylinder": 0, "box": 1}[mode], int(nthreads), _p(counts), _p(t))
     return counts, t
 
 

@@ -740,9 +740,10 @@ static double box_search(const v4 Q[4], int depth, double tmax, int64_t *count)
  * traversal), mode 1 boxes.  counts: n_ray int64; t_out (nullable): the
  * closest hit found (inf on a miss).
  */
-void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
-                    const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
-                    int depth, int mode, int nthreads, int64_t *counts, double *t_out)
+static void ray_counts_impl(const float *rays_f, const double *rays_d, int64_t n_ray, const int32_t *row_ptr,
+                            const int32_t *seg_idx, const double *piece_cp, const int32_t *piece_begin,
+                            const int32_t *piece_level, int depth, int mode, int nthreads, int64_t *counts,
+                            double *t_out)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -751,7 +752,7 @@ void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, co
 #endif
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n_ray; ++i) {
-        ray_t r = make_ray_f(rays + 8 * i);
+        ray_t r = rays_f ? make_ray_f(rays_f + 8 * i) : make_ray_d(rays_d + 7 * i);
         if (mode == 1) duff_frame(r.w, r.e1, r.e2);
         double best = r.tmax;
         int64_t n = 0;
@@ -774,6 +775,23 @@ void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, co
         counts[i] = n;
         if (t_out) t_out[i] = best < r.tmax ? best : INFINITY;
     }
+}
+
+void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+                    const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+                    int depth, int mode, int nthreads, int64_t *counts, double *t_out)
+{
+    ray_counts_impl(rays, NULL, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, depth, mode,
+                    nthreads, counts, t_out);
+}
+
+/* The same with rays given in double precision (7 doubles: o, w, t_max). */
+void orc_ray_counts_d(const double *rays7, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+                      const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+                      int depth, int mode, int nthreads, int64_t *counts, double *t_out)
+{
+    ray_counts_impl(NULL, rays7, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, depth, mode,
+                    nthreads, counts, t_out);
 }
 
 /* ------------------------------------------------------ quadratic curves */

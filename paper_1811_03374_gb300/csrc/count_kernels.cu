@@ -15,7 +15,8 @@
 //     again (one count) when taken up after the first one's subtree.  The
 //     search does not end at the first leaf hit; a leaf whose box is hit
 //     takes the capped-cylinder leaf test of Sec. 3.3.
-// Handles whose segments are single level-0 pieces only.
+// A pre-split segment's pieces are searched in order, each to depth - level
+// (its leaves are the unsplit curve's), with the closest hit so far as t_max.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -84,11 +85,10 @@ __device__ __forceinline__ bool leaf_test(const Node& c, float tmax, float& t) {
 // best; adds its box tests to n and returns the closest t (best if none).
 // A leaf counts only its box test; the cap keeps a runaway ray finite.
 template <bool FAST>
-__device__ float box_search(const Node& R, int depth, float best, uint64_t& n, uint32_t* status) {
+__device__ float box_search(const Node& R, uint32_t min_size, float best, uint64_t& n, uint32_t* status) {
   float zmin;
   ++n;
   if (!box_hit(R, best, zmin)) return best;
-  const uint32_t min_size = 1u << piece_min_size_shift(depth, 0);
   Node c = R;
   uint32_t bits = 0, start = 0, size = kRootSize;
   uint64_t steps = 0;
@@ -114,7 +114,7 @@ __device__ float box_search(const Node& R, int depth, float best, uint64_t& n, u
     }
     // take up the deepest deferred sibling, tested again against t_max
     while (!next && bits != 0u) {
-      jump_up(bits, start, size);
+      take_pending(bits, start, size);
       recompute(R, start, size, c);
       ++n;
       next = box_hit(c, best, zmin);
@@ -146,26 +146,29 @@ __global__ void __launch_bounds__(kCountBlock) k_counts(const TraceArgs a, uint3
         atomicOr(a.status, FX_DEV_BAD_INDEX);
         continue;
       }
-      if (BOX) {
+      const int32_t pb = a.identity ? s : __ldg(a.piece_begin + s);
+      const int32_t pe = a.identity ? s + 1 : __ldg(a.piece_begin + s + 1);
+      for (int32_t k = pb; k < pe; ++k) {
+        const int32_t info = a.identity ? 0 : __ldg(a.piece_info + k);
         PairState st;
-        begin_piece<FAST>(st, a.piece, s, rf, 0, a.depth, best);
-        best = box_search<FAST>(st.R, a.depth, best, n, a.status);
-      } else {
-        PairState st;
-        begin_piece<FAST>(st, a.piece, s, rf, 0, a.depth, best);
-        unsigned long long nd = 0, nb = 0;
-        for (;;) {
-          float t;
-          const StepResult res = node_step<FAST, false>(st, best, t, nd, nb);
-          ++n;
-          if (res == kStepLeaf) {
-            if (t < best) best = t;
-            break;
-          }
-          if (res == kStepDone) break;
-          if (st.iters >= iter_cap(a.depth)) {
-            atomicOr(a.status, FX_DEV_ITER_LIMIT);
-            break;
+        begin_piece<FAST>(st, a.piece, k, rf, info, a.depth, best);
+        if (BOX) {
+          best = box_search<FAST>(st.R, st.min_size, best, n, a.status);
+        } else {
+          unsigned long long nd = 0, nb = 0;
+          for (;;) {
+            float t;
+            const StepResult res = node_step<FAST, false>(st, best, t, nd, nb);
+            ++n;
+            if (res == kStepLeaf) {
+              if (t < best) best = t;
+              break;
+            }
+            if (res == kStepDone) break;
+            if (st.iters >= iter_cap(a.depth)) {
+              atomicOr(a.status, FX_DEV_ITER_LIMIT);
+              break;
+            }
           }
         }
       }

@@ -1,12 +1,15 @@
 """Per-ray pruning-test counts on the GPU (intersect_counts, Fig. 8) against
-the FP64 oracle's, through the C ABI: oriented cylinders and ray-frame boxes,
-on single fibers of three curvature classes, the depth sweep and the hair
-patch.  The counts are integers decided by floating-point tests, which FP32
-and FP64 settle differently only for rays grazing a bounding volume: equal
-counts on at least 99 % of the rays (98 % for boxes, whose searches are long
-at depth; within 2 on hair rows of about 190 candidates) and totals within
-1 %.  The boxes are aligned to Duff et al.'s frame on both sides (a box in
-the ray's frame depends on the frame's rotation about the ray)."""
+the FP64 oracle's, ray by ray, through the C ABI: oriented cylinders and
+ray-frame boxes, on single fibers of three curvature classes, the depth
+sweep (the curved class pre-split), the tiny workload (pre-split, 16
+candidates per ray) and the hair patch.  A count sums integer outcomes of
+floating-point tests over a ray's row, so every ray's count must equal the
+oracle's, or, where FP32 settled a test on a grazing bounding volume the
+other way, equal the oracle's count for the same ray shifted sideways
+within the FP32 resolution band (tests/_parity.py); such rays stay a small
+share.  The boxes are aligned to Duff et al.'s frame on both sides (a box in
+the ray's frame depends on the frame's rotation about the ray).  With
+FX_REPORT=<path> set, every comparison appends its counts."""
 import numpy as np
 import pytest
 
@@ -27,39 +30,56 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _compare(case, depth, mode, flags=0, eq=0.99, slack=0, total=0.01):
+def _compare(case, depth, mode, flags=0, max_band_frac=2e-3, **rec):
     pieces = O.presplit(case["cps"])
     ref, _ = O.ray_counts(case, depth, mode, pieces)
     fib = F.Fibers(case["cps"])
     got = F.intersect_counts(fib, case["rays"], case["row_ptr"], case["seg_idx"], depth, boxes=mode == "box",
-                             flags=flags).cpu().numpy()
-    assert fib.status() == 0
+                             flags=flags).cpu().numpy().astype(np.int64)
+    assert fib.status() & ~F.FX_DEV_UNSUPPORTED == 0
     fib.close()
-    same = np.mean(np.abs(got - ref) <= slack)
-    tot = abs(got.sum() - ref.sum()) / max(1, ref.sum())
-    assert same >= eq and tot <= total, (mode, depth, same, tot)
-    return dict(mean=float(got.mean()), max=int(got.max()), p99=float(np.percentile(got, 99)), same=float(same),
-                total_rel_diff=float(tot))
+    diff = np.nonzero(got != ref)[0]
+    band = P.band_counts(case, diff, got, depth, mode, pieces)
+    fail = diff[~band]
+    st = dict(n=len(got), equal=int(len(got) - len(diff)), band=int(band.sum()), fail=int(len(fail)),
+              mean=float(got.mean()), max=int(got.max()), p99=float(np.percentile(got, 99)))
+    P.report(dict(test="counts", depth=depth, mode=mode, math="fast" if flags & F.FX_FAST_MATH else "ieee",
+                  **rec, **st))
+    assert len(fail) == 0, (mode, depth, fail[:8].tolist(), got[fail[:8]].tolist(), ref[fail[:8]].tolist())
+    assert len(diff) <= max_band_frac * len(got), (mode, depth, len(diff))
+    return st
 
 
 @pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
 @pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
 def test_counts_single_fiber(klass, flags):
     case = I.single_fiber_case(klass, 8192)
-    if O.presplit(case["cps"])["seg"].shape[0] != 1:
-        pytest.skip("the fiber is pre-split")
     for depth in (2, 8, 12, 16):
-        for mode, eq in (("cylinder", 0.99), ("box", 0.98)):
-            st = _compare(case, depth, mode, flags, eq)
-            P.report(dict(test="counts", case="single_" + klass, depth=depth, mode=mode,
-                          math="fast" if flags else "ieee", **st))
+        for mode in ("cylinder", "box"):
+            # box searches are long at depth: more tests, more grazing ones
+            _compare(case, depth, mode, flags, 2e-3 if mode == "cylinder" else 1e-2, case="single_" + klass)
 
 
-def test_counts_depth_sweep():
-    case = I.sweep_case("moderate", 4096)
+@pytest.mark.parametrize("klass", list(I.SWEEP_JITTER))
+def test_counts_depth_sweep(klass):
+    # the curved class holds pre-split segments: each piece searched to
+    # depth - level
+    case = I.sweep_case(klass, 4096)
     for depth in (4, 12):
-        for mode, eq in (("cylinder", 0.99), ("box", 0.98)):
-            _compare(case, depth, mode, 0, eq)
+        for mode in ("cylinder", "box"):
+            _compare(case, depth, mode, 0, 2e-3 if mode == "cylinder" else 1e-2, case="sweep_" + klass)
+
+
+@pytest.mark.parametrize("flags", [0, F.FX_FAST_MATH], ids=["ieee", "fast"])
+def test_counts_tiny_presplit(flags):
+    # 16 random cubics, most of them pre-split, 16 candidates per ray
+    case = I.tiny_case()
+    fib = F.Fibers(case["cps"])
+    assert fib.info()["n_presplit"] > 0
+    fib.close()
+    for depth in (4, 8):
+        for mode in ("cylinder", "box"):
+            _compare(case, depth, mode, flags, 5e-3 if mode == "cylinder" else 2e-2, case="tiny")
 
 
 def test_counts_hair():
@@ -67,16 +87,6 @@ def test_counts_hair():
     counts = np.diff(case["row_ptr"])
     idx = np.sort(np.random.default_rng(9).choice(np.nonzero(counts > 0)[0], 2000, replace=False))
     sub = I.subsample_rays(case, idx)
-    # a hair ray sums about 190 traversals: one decision settled differently
-    # anywhere in the row moves its count, so each count is held to within 2
-    st = _compare(sub, 15, "cylinder", F.FX_FAST_MATH, eq=0.99, slack=2, total=0.001)
-    P.report(dict(test="counts", case="hair", depth=15, mode="cylinder", math="fast", **st))
-
-
-def test_counts_refuse_presplit_handles():
-    case = I.tiny_case(n_ray=64)
-    fib = F.Fibers(case["cps"])
-    assert fib.info()["n_presplit"] > 0
-    with pytest.raises(F.FiberxError):
-        F.intersect_counts(fib, case["rays"], case["row_ptr"], case["seg_idx"], 8)
-    fib.close()
+    # a hair ray sums about 190 candidates' searches: a grazing test anywhere
+    # in the row moves its count
+    _compare(sub, 15, "cylinder", F.FX_FAST_MATH, 2e-2, case="hair")

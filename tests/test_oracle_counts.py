@@ -74,3 +74,43 @@ def test_fig8_boxes_grow_exponentially_cylinders_linearly():
         assert box[k] >= 2.0 * box[k - 1], box          # at least x2 per 3 levels
         assert cyl[k] - cyl[k - 1] <= 3.0 * 1.5, cyl     # about one per level
     assert box[-1] > 20 * cyl[-1]
+
+
+@pytest.mark.parametrize("depth", [3, 9, 16])
+def test_cylinder_counts_on_presplit_segments(depth):
+    # a pre-split segment's count is the sum of its pieces' node tests, each
+    # piece traversed to depth - level with the closest hit so far as t_max
+    # (its leaves are the unsplit curve's)
+    case = I.sweep_case("curved", 300, forced_hits=True)
+    pieces = O.presplit(case["cps"])
+    counts, t = O.ray_counts(case, depth, "cylinder", pieces)
+    n_split = 0
+    for i in range(300):
+        b, e = pieces["begin"][i], pieces["begin"][i + 1]
+        r7 = O.ray7_from_packed(case["rays"][i])
+        best, n = r7[6], 0
+        for k in range(b, e):
+            r7k = r7.copy()
+            r7k[6] = best
+            h = O.intersect(r7k, pieces["cp"][k], max(depth - int(pieces["level"][k]), 0))
+            n += h.nodes
+            if h.hit and h.t < best:
+                best = h.t
+        assert counts[i] == n
+        assert (np.isfinite(best) and abs(t[i] - best) <= 1e-12 * best) or (np.isinf(best) and np.isinf(t[i]))
+        n_split += e - b > 1
+    assert n_split > 30
+
+
+@pytest.mark.parametrize("mode", ["cylinder", "box"])
+def test_counts_with_double_rays_equal_float_rays(mode):
+    # the double-precision ray entry (used to shift rays by less than an FP32
+    # step) gives the float entry's counts on the same rays
+    case = I.tiny_case(n_ray=512)
+    pieces = O.presplit(case["cps"])
+    c_f, t_f = O.ray_counts(case, 8, mode, pieces)
+    r7 = np.stack([O.ray7_from_packed(r) for r in case["rays"]])
+    c_d, t_d = O.ray_counts_d(r7, case["row_ptr"], case["seg_idx"], 8, mode, pieces)
+    np.testing.assert_array_equal(c_d, c_f)
+    np.testing.assert_array_equal(t_d, t_f)
+    assert c_f.sum() > 512
