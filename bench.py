@@ -86,7 +86,91 @@ def emit(obj, args):
 
 # ----------------------------------------------------------------- clocks
 
+class NvmlClocks:
+    """SM clock and clock-event reasons of one GPU, sampled from a thread
+    about every `period` seconds between start() and stop() through NVML's
+    read-only queries (libnvidia-ml via ctypes; nothing is set).  A timed
+    region of a few milliseconds still gets several samples."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device, period=0.0005):
+        import ctypes
+        self.ok = False
+        self.samples = []
+        self.period = period
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            got = False
+            try:
+                import torch
+                uuid = "GPU-" + str(torch.cuda.get_device_properties(torch_device).uuid)
+                got = nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0
+            except Exception:
+                got = False
+            if not got:
+                vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+                idx = int(vis.split(",")[torch_device]) if vis and vis.split(",")[0].isdigit() else torch_device
+                got = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) == 0
+            if not got:
+                return
+            reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self._nv, self._h, self._reasons, self._ct = nv, h, reasons, ctypes
+            mx = ctypes.c_uint(0)
+            self.max_mhz = float(mx.value) if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 else None
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _sample(self):
+        ct = self._ct
+        mhz, rs = ct.c_uint(0), ct.c_ulonglong(0)
+        if self._nv.nvmlDeviceGetClockInfo(self._h, 1, ct.byref(mhz)) == 0 and \
+                self._reasons(self._h, ct.byref(rs)) == 0:
+            self.samples.append((time.perf_counter(), float(mhz.value), int(rs.value)))
+
+    def start(self):
+        import threading
+        if not self.ok:
+            return self
+        self._stop = threading.Event()
+
+        def loop():
+            while not self._stop.is_set():
+                self._sample()
+                time.sleep(self.period)
+        self._thread = threading.Thread(target=loop, daemon=True)
+        self._thread.start()
+        return self
+
+    def stop(self, ms_per_step=None):
+        if not self.ok:
+            return None
+        self._stop.set()
+        self._thread.join()
+        self._sample()  # at least one sample at the end of the region
+        if not self.samples:
+            return None
+        sm = np.array([x[1] for x in self.samples])
+        seen = 0
+        for x in self.samples:
+            seen |= x[2]
+        out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
+               "sm_mhz_min": float(sm.min()), "sm_mhz_max_seen": float(sm.max()),
+               "reasons": sorted(v for k, v in self.REASONS.items() if seen & k), "source": "nvml"}
+        if ms_per_step is not None:
+            # time x clock: thousands of SM cycles per step at the median clock
+            out["kcycles_per_step_at_median"] = ms_per_step * out["sm_mhz"]
+        return out
+
+
 class ClockSampler:
+    """nvidia-smi sampling (100 ms period): the fallback where NVML cannot be
+    loaded."""
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
@@ -105,7 +189,7 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, ms_per_step=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -132,8 +216,17 @@ class ClockSampler:
             for n, v in zip(names, r[2][1:]):
                 if v.lower() == "active":
                     reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
-                "samples": len(rows), "reasons": sorted(reasons)}
+        out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
+               "samples": len(rows), "reasons": sorted(reasons), "source": "nvidia-smi"}
+        if ms_per_step is not None:
+            out["kcycles_per_step_at_median"] = ms_per_step * out["sm_mhz"]
+        return out
+
+
+def clock_sampler(local):
+    """NVML sampling where it loads, else nvidia-smi's."""
+    c = NvmlClocks(local)
+    return c.start() if c.ok else ClockSampler(local)
 
 
 # ------------------------------------------------------------- workload
@@ -339,7 +432,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local) if rank == 0 else None
+    clocks = clock_sampler(local) if rank == 0 else None
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for i in range(args.steps):
@@ -349,8 +442,8 @@ def main():
             ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    clk = clocks.stop() if clocks else None
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    clk = clocks.stop(float(np.mean(ms))) if clocks else None
     ms_step = max_over_ranks(float(np.mean(ms)), dist, dev)
     if dist:
         dist.barrier()

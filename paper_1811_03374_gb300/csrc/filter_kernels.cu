@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kActiveBlock, 6) k_active(const TraceArgs a, c
       } else if (bits == 0u) {
         piece_done = true;
       } else {
-        jump_up(bits, start, size);
+        take_pending(bits, start, size);
         Node R;
         rotate_piece(a.piece, piece, rf, R);  // the root node, rebuilt
         recompute(R, start, size, c);

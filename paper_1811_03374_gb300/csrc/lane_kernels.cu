@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kLaneBlock, 6) k_lane(const TraceArgs a, int c
       } else if (st.bits == 0u) {
         piece_done = true;
       } else {
-        jump_up(st.bits, st.start, st.size);
+        take_pending(st.bits, st.start, st.size);
         Node R;
         to_local(a.piece, st.piece, rf, R);  // the root node, rebuilt
         recompute(R, st.start, st.size, st.c);

@@ -235,7 +235,7 @@ __device__ __forceinline__ bool ray_walk(const TraceArgs& a, int64_t r, RayWalk&
         } else if (bits == 0u) {
           break;
         } else {
-          jump_up(bits, start, size);
+          take_pending(bits, start, size);
           recompute(R, start, size, c);
           tmax = pair_tmax;
           slab_ok = false;

@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
       } else if (bits == 0u) {
         piece_done = true;
       } else {
-        jump_up(bits, start, size);
+        take_pending(bits, start, size);
         Node R;
         to_local(s_cur, R);  // the root node, rebuilt
         recompute(R, start, size, c);

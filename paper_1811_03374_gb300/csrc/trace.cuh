@@ -225,12 +225,19 @@ __device__ __forceinline__ void descend(Node& c, float c0, float c1, float& tmin
   if (go_right) start |= size;
 }
 
-// jump_up (Sec. 3.3): go to the sibling at the deepest level whose bit is set.
-__device__ __forceinline__ void jump_up(uint32_t& bits, uint32_t& start, uint32_t& size) {
-  size = bits & (0u - bits);
-  start ^= size;
-  bits ^= size;
-  start &= ~(size - 1u);
+// Backtracking without a stack (Sec. 3.3).  The search is a depth-first
+// descent whose stack would only ever hold "the other child" of some
+// ancestors; one bit per level (set at the level's node size) records which
+// ancestors still owe that visit.  The node to resume is the other child at
+// the deepest such level: with h its size (the lowest pending bit), its
+// interval begins at the start of the current node's ancestor of size 2h,
+// plus h if the current path took that ancestor's left child.  The bit is
+// consumed; the node's geometry is recomputed by the caller.
+__device__ __forceinline__ void take_pending(uint32_t& pending, uint32_t& start, uint32_t& size) {
+  const uint32_t h = pending & (0u - pending);
+  start = (start & (0u - (h << 1))) | (~start & h);
+  pending &= pending - 1u;
+  size = h;
 }
 
 // Node of the interval [u0, u0 + h] recomputed from the local root node R
@@ -345,21 +352,23 @@ __device__ __forceinline__ StepResult node_step(PairState& st, float pair_tmax, 
   const bool over = cylinder<FAST>(st.c.p, st.c.d, r, c0, c1) &&
                     fmaxf(c0, st.tmin) <= fminf(c1, st.tmax);
   ++st.iters;
-  if (over && st.size <= st.min_size) {
-    t = fmaxf(c0, st.tmin);
-    return kStepLeaf;
+  if (!over) {
+    // pruned: resume at the deepest pending sibling, or the piece is done
+    if (st.bits == 0u) return kStepDone;
+    take_pending(st.bits, st.start, st.size);
+    recompute(st.R, st.start, st.size, st.c);
+    slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
+    if (COUNT) ++nb;
+    return kStepContinue;
   }
-  if (over) {
+  if (st.size > st.min_size) {
     descend<FAST>(st.c, c0, c1, st.tmin, st.tmax, st.bits, st.start, st.size);
     if (COUNT) ++nd;
     return kStepContinue;
   }
-  if (st.bits == 0u) return kStepDone;
-  jump_up(st.bits, st.start, st.size);
-  recompute(st.R, st.start, st.size, st.c);
-  slab<FAST>(st.c, pair_tmax, st.tmin, st.tmax);
-  if (COUNT) ++nb;
-  return kStepContinue;
+  // a leaf whose capped cylinder the ray enters: the hit (instant termination)
+  t = fmaxf(c0, st.tmin);
+  return kStepLeaf;
 }
 
 }  // namespace fx
