@@ -71,6 +71,8 @@ def lib():
             L.orc_ray_counts.restype = None
             L.orc_ray_counts_d.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp]
             L.orc_ray_counts_d.restype = None
+            L.orc_ray_counts_amb.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp]
+            L.orc_ray_counts_amb.restype = None
             L.orc_presplit_d.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp, i64]
             L.orc_presplit_d.restype = i64
             L.orc_valid_quadratic.argtypes = [vp]; L.orc_valid_quadratic.restype = i32
@@ -225,6 +227,23 @@ def ray_counts(case, depth, mode, pieces=None, nthreads=0):
     lib().orc_ray_counts(_p(rays), n, _p(rp), _p(si), _p(pc), _p(pieces["begin"]), _p(pieces["level"]),
                          int(depth), {"cylinder": 0, "box": 1}[mode], int(nthreads), _p(counts), _p(t))
     return counts, t
+
+
+def ray_counts_amb(case, depth, mode, delta, pieces=None, nthreads=0):
+    """ray_counts() and, per ray, whether any decision of its search lies
+    within delta[i] (a length; per ray) of flipping under a sideways move of
+    the ray: (counts int64 [n_ray], ambiguous bool [n_ray])."""
+    if pieces is None:
+        pieces = presplit(case["cps"])
+    rays, rp, si, pc = _ws(case, pieces)
+    n = rays.shape[0]
+    counts = np.zeros(n, np.int64)
+    amb = np.zeros(n, np.int32)
+    dl = np.ascontiguousarray(np.broadcast_to(np.asarray(delta, np.float64), (n,)))
+    lib().orc_ray_counts_amb(_p(rays), n, _p(rp), _p(si), _p(pc), _p(pieces["begin"]), _p(pieces["level"]),
+                             int(depth), {"cylinder": 0, "box": 1}[mode], int(nthreads), _p(dl), _p(counts),
+                             _p(amb))
+    return counts, amb.astype(bool)
 
 
 def ray_counts_d(rays7, row_ptr, seg_idx, depth, mode, pieces, nthreads=0):

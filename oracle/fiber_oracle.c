@@ -279,6 +279,88 @@ static void node_of_points(const v4 Q[4], node_t *c)
     c->t1 = sub4(Q[3], Q[2]);
 }
 
+/* ------------------------------------------------ FP32-band probe */
+
+/*
+ * Decisions within the FP32 band (used only by orc_ray_counts_amb; the
+ * traversal's own decisions are unchanged).  A decision is "in the band" of
+ * a ray when moving the ray sideways by up to delta could flip it: each probe
+ * below re-evaluates a decision with the node translated in the ray frame by
+ * delta in 8 directions of the xy plane (a sideways shift of the ray by
+ * delta is a shift of everything else by -delta), or compares the margin of
+ * a comparison along the ray with delta.  The first such decision of a ray
+ * sets its flag.  NULL context: no probing.
+ */
+typedef struct { double delta; int amb; } probe_t;
+static _Thread_local probe_t *g_probe = NULL;
+
+static node_t shifted(const node_t *c, double dx, double dy)
+{
+    node_t s = *c;
+    s.p.x -= dx;
+    s.p.y -= dy;
+    return s;
+}
+
+/* A cylinder node test (Sec. 3.2): the overlap decision with the inherited
+ * interval [tmin, tmax], moved by how far the node's own cropping planes move,
+ * and, for an inner node that is hit, the partition decisions (near child,
+ * both children). */
+static void probe_node(const node_t *c, double tmin, double tmax, double ray_tmax, int over, int leaf)
+{
+    if (!g_probe || g_probe->amb) return;
+    double dl = g_probe->delta, r = cons_radius(c), lo0, hi0, c0 = 0, c1 = 0, tp0 = 0;
+    slab(c, ray_tmax, &lo0, &hi0);
+    int gr0 = 0, both0 = 0;
+    v4 dp, tc;
+    split_terms(c, &dp, &tc);
+    if (over && !leaf) {
+        cylinder(c->p, c->d, r, &c0, &c1);
+        if (plane_t(add4(c->p, dp), tc, &tp0)) {
+            gr0 = (tp0 > c0) != (tc.z > 0.0);
+            both0 = (c0 < tp0) && (c1 > tp0);
+        } else {
+            gr0 = -dot3(add4(c->p, dp), tc) >= 0.0;
+        }
+    }
+    for (int k = 0; k < 8; ++k) {
+        double a = k * (3.14159265358979323846 / 4.0);
+        node_t s = shifted(c, dl * cos(a), dl * sin(a));
+        double lo, hi, s0, s1;
+        slab(&s, ray_tmax, &lo, &hi);
+        double ilo = tmin + ((isfinite(lo) && isfinite(lo0)) ? lo - lo0 : 0.0);
+        double ihi = tmax + ((isfinite(hi) && isfinite(hi0)) ? hi - hi0 : 0.0);
+        int ov = cylinder(s.p, s.d, r, &s0, &s1) && dmax(s0, ilo) <= dmin(s1, ihi);
+        if (ov != over) { g_probe->amb = 1; return; }
+        /* the interval's far end is the closest hit so far (the t_max of the
+           search), itself a result of earlier tests: the overlap is in the
+           band when its margin against that bound is within delta */
+        if (ov && ihi >= ray_tmax && isfinite(ray_tmax) && dmin(s1, ihi) - dmax(s0, ilo) <= dl) {
+            g_probe->amb = 1;
+            return;
+        }
+        if (over && !leaf) {
+            double tp;
+            int gr, both = 0;
+            if (plane_t(add4(s.p, dp), tc, &tp)) {
+                gr = (tp > s0) != (tc.z > 0.0);
+                both = (s0 < tp) && (s1 > tp);
+            } else {
+                gr = -dot3(add4(s.p, dp), tc) >= 0.0;
+            }
+            if (gr != gr0 || both != both0) { g_probe->amb = 1; return; }
+        }
+    }
+}
+
+/* A comparison of two distances along the ray (a hit against the closest so
+ * far, two boxes' near ends): in the band when they are within delta. */
+static void probe_order(double a, double b)
+{
+    if (!g_probe || g_probe->amb || !isfinite(a) || !isfinite(b)) return;
+    if (fabs(a - b) <= g_probe->delta) g_probe->amb = 1;
+}
+
 /* ----------------------------------------------------------- traversal */
 
 /*
@@ -315,6 +397,7 @@ static void traverse(const v4 Q[4], int depth, double ray_tmax, orc_hit *h)
         double r = cons_radius(&c), c0 = 0.0, c1 = 0.0;
         h->nodes++;
         int over = cylinder(c.p, c.d, r, &c0, &c1) && dmax(c0, tmin) <= dmin(c1, tmax);
+        probe_node(&c, tmin, tmax, ray_tmax, over, size <= min_size);
         if (over) {
             if (size <= min_size) {
                 t = dmax(c0, tmin);
@@ -673,6 +756,13 @@ static int box_hit(const node_t *c, double tmax)
             hi[a] = dmax(hi[a], v[a] + q[k].w);
         }
     }
+    if (g_probe && !g_probe->amb) {  /* a face of the box within delta of the ray */
+        double dl = g_probe->delta;
+        if (fabs(lo[0]) <= dl || fabs(hi[0]) <= dl || fabs(lo[1]) <= dl || fabs(hi[1]) <= dl ||
+            fabs(hi[2]) <= dl)
+            g_probe->amb = 1;
+        probe_order(lo[2], tmax);
+    }
     return lo[0] <= 0.0 && hi[0] >= 0.0 && lo[1] <= 0.0 && hi[1] >= 0.0 && hi[2] >= 0.0 && lo[2] <= tmax;
 }
 
@@ -691,7 +781,9 @@ static int leaf_test(const node_t *c, double tmax, double *t)
     double tmin, tm, c0, c1;
     slab(c, tmax, &tmin, &tm);
     double r = cons_radius(c);
-    if (!(cylinder(c->p, c->d, r, &c0, &c1) && dmax(c0, tmin) <= dmin(c1, tm))) return 0;
+    int over = cylinder(c->p, c->d, r, &c0, &c1) && dmax(c0, tmin) <= dmin(c1, tm);
+    probe_node(c, tmin, tm, tmax, over, 1);
+    if (!over) return 0;
     *t = dmax(c0, tmin);
     return *t < tmax;
 }
@@ -712,6 +804,7 @@ static void box_visit(const node_t *c, uint32_t size, uint32_t min_size, double 
     int hl = box_hit(&L, *best), hr = box_hit(&R, *best);
     if (hl && hr) {
         int right_first = box_zmin(&R) < box_zmin(&L);
+        probe_order(box_zmin(&R), box_zmin(&L));
         const node_t *a = right_first ? &R : &L, *b = right_first ? &L : &R;
         box_visit(a, size >> 1, min_size, best, count);
         *count += 1;
@@ -743,7 +836,7 @@ static double box_search(const v4 Q[4], int depth, double tmax, int64_t *count)
 static void ray_counts_impl(const float *rays_f, const double *rays_d, int64_t n_ray, const int32_t *row_ptr,
                             const int32_t *seg_idx, const double *piece_cp, const int32_t *piece_begin,
                             const int32_t *piece_level, int depth, int mode, int nthreads, int64_t *counts,
-                            double *t_out)
+                            double *t_out, const double *delta, int32_t *amb)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -756,6 +849,8 @@ static void ray_counts_impl(const float *rays_f, const double *rays_d, int64_t n
         if (mode == 1) duff_frame(r.w, r.e1, r.e2);
         double best = r.tmax;
         int64_t n = 0;
+        probe_t pr = {delta ? delta[i] : 0.0, 0};
+        g_probe = delta ? &pr : NULL;
         for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
             int32_t s = seg_idx[j];
             for (int32_t k = piece_begin[s]; k < piece_begin[s + 1]; ++k) {
@@ -774,6 +869,8 @@ static void ray_counts_impl(const float *rays_f, const double *rays_d, int64_t n
         }
         counts[i] = n;
         if (t_out) t_out[i] = best < r.tmax ? best : INFINITY;
+        if (amb) amb[i] = pr.amb;
+        g_probe = NULL;
     }
 }
 
@@ -782,7 +879,7 @@ void orc_ray_counts(const float *rays, int64_t n_ray, const int32_t *row_ptr, co
                     int depth, int mode, int nthreads, int64_t *counts, double *t_out)
 {
     ray_counts_impl(rays, NULL, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, depth, mode,
-                    nthreads, counts, t_out);
+                    nthreads, counts, t_out, NULL, NULL);
 }
 
 /* The same with rays given in double precision (7 doubles: o, w, t_max). */
@@ -791,7 +888,23 @@ void orc_ray_counts_d(const double *rays7, int64_t n_ray, const int32_t *row_ptr
                       int depth, int mode, int nthreads, int64_t *counts, double *t_out)
 {
     ray_counts_impl(NULL, rays7, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, depth, mode,
-                    nthreads, counts, t_out);
+                    nthreads, counts, t_out, NULL, NULL);
+}
+
+/*
+ * orc_ray_counts with, per ray, a flag: 1 if any decision of its search lies
+ * within delta[i] of flipping under a sideways move of the ray (the probes
+ * above).  A count on such a ray may legitimately come out differently in
+ * lower precision; on any other ray every decision has a margin of at least
+ * delta[i].  Rays as 8 floats (the workload's FP32 rays).
+ */
+void orc_ray_counts_amb(const float *rays, int64_t n_ray, const int32_t *row_ptr, const int32_t *seg_idx,
+                        const double *piece_cp, const int32_t *piece_begin, const int32_t *piece_level,
+                        int depth, int mode, int nthreads, const double *delta, int64_t *counts,
+                        int32_t *amb)
+{
+    ray_counts_impl(rays, NULL, n_ray, row_ptr, seg_idx, piece_cp, piece_begin, piece_level, depth, mode,
+                    nthreads, counts, NULL, delta, amb);
 }
 
 /* ------------------------------------------------------ quadratic curves */

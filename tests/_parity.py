@@ -64,6 +64,11 @@ TOL_U = 1e-5
 EPS32 = 2.0 ** -24
 K_FRAME = 22.0
 SCALES = tuple(2.0 ** -k for k in range(17))
+# the second, finer search (results the first one leaves unexplained): 32
+# directions, scales delta * 2^(-k/8) down to delta * 2^-12
+FINE_DIRS = 32
+FINE_SCALES = tuple(2.0 ** (-k / 8.0) for k in range(97))
+FINE_MAX = 200
 
 
 def _bez(cp, u):
@@ -121,12 +126,53 @@ def _perp(w):
     return e1, e2
 
 
+def _shift_search(case, rays8, cands, g, depth, pieces, delta, T, dirs_of, scales):
+    """Oracle results of the rays shifted by delta * scale along each of
+    dirs_of(e1, e2); returns (passed [m], smallest passing shift / (2^-24 T))."""
+    m = len(cands)
+    rays = rays8.astype(np.float64)
+    o_, w = rays[:, :3], rays[:, 4:7]
+    w = w / np.linalg.norm(w, axis=1, keepdims=True)
+    e1, e2 = _perp(w)
+    dirs = dirs_of(e1, e2)
+    tmax = rays[:, 3]
+    sub_rays, rows, segs = [], [0], []
+    for sc in scales:
+        for dv in dirs:
+            # double-precision rays: shifts far below an FP32 step of |o| stay exact
+            sub_rays.append(np.concatenate([o_ + (delta * sc)[:, None] * dv, w, tmax[:, None]], axis=1))
+            for c in cands:
+                segs.append(c)
+                rows.append(rows[-1] + len(c))
+    ref = O.closest_d(np.concatenate(sub_rays), np.array(rows, dtype=np.int32),
+                      np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32),
+                      depth, pieces)
+    tol_u = u_tolerance(case, rays8, g["seg"], g["t"], g["u"])
+    ok = np.zeros(m, dtype=bool)
+    shift = np.full(m, np.inf)
+    k = 0
+    for sc in scales:
+        for _ in dirs:
+            sl = slice(k * m, (k + 1) * m)
+            hit = strict_ok(g["t"], g["u"], g["seg"], ref["t"][sl], ref["u"][sl], ref["seg"][sl], tol_u)
+            shift = np.where(hit, np.minimum(shift, delta * sc / (EPS32 * np.maximum(T, 1e-30))), shift)
+            ok |= hit
+            k += 1
+    return ok, shift
+
+
 def band_check(case, rays8, cands, g, o, depth, pieces):
     """For results that failed the strict rule: rays8 [m, 8] their rays,
     cands a list of m candidate-id arrays (a ray's row, or one pair's
     segment), g / o dicts of the GPU / oracle results (t, u, seg) per
     result.  Returns (passed [m] bool, smallest passing shift in units of
-    2^-24 T [m], inf where none)."""
+    2^-24 T [m], inf where none).
+
+    The first search takes 8 directions and factors of 2; results it leaves
+    unexplained (at most FINE_MAX of them) are searched again with 32
+    directions and factors of 2^(1/8).  A ray nearly parallel to its fiber
+    needs the finer one: there u moves along the fiber by the shift over
+    tan(angle), so only a narrow range of shifts reproduces a u to 1e-5."""
     m = len(cands)
     if m == 0:
         return np.zeros(0, bool), np.zeros(0)
@@ -145,32 +191,19 @@ def band_check(case, rays8, cands, g, o, depth, pieces):
         T[has] = frame_extent(case["cps"], rays8[has], seg[has])
     T = np.where(has, T, np.linalg.norm(o_, axis=1))
     delta = 1e-4 * r + K_FRAME * EPS32 * T
-    e1, e2 = _perp(w)
     s2 = np.sqrt(0.5)
-    dirs = [e1, -e1, e2, -e2, s2 * (e1 + e2), s2 * (e1 - e2), s2 * (-e1 + e2), s2 * (-e1 - e2)]
-    tmax = rays[:, 3]
-    sub_rays, rows, segs = [], [0], []
-    for sc in SCALES:
-        for dv in dirs:
-            # double-precision rays: shifts far below an FP32 step of |o| stay exact
-            sub_rays.append(np.concatenate([o_ + (delta * sc)[:, None] * dv, w, tmax[:, None]], axis=1))
-            for c in cands:
-                segs.append(c)
-                rows.append(rows[-1] + len(c))
-    ref = O.closest_d(np.concatenate(sub_rays), np.array(rows, dtype=np.int32),
-                      np.concatenate(segs).astype(np.int32) if segs else np.zeros(0, np.int32),
-                      depth, pieces)
-    tol_u = u_tolerance(case, rays8, g["seg"], g["t"], g["u"])
-    ok = np.zeros(m, dtype=bool)
-    shift = np.full(m, np.inf)
-    k = 0
-    for sc in SCALES:
-        for _ in dirs:
-            sl = slice(k * m, (k + 1) * m)
-            hit = strict_ok(g["t"], g["u"], g["seg"], ref["t"][sl], ref["u"][sl], ref["seg"][sl], tol_u)
-            shift = np.where(hit, np.minimum(shift, delta * sc / (EPS32 * np.maximum(T, 1e-30))), shift)
-            ok |= hit
-            k += 1
+    ok, shift = _shift_search(case, rays8, cands, g, depth, pieces, delta, T,
+                              lambda e1, e2: [e1, -e1, e2, -e2, s2 * (e1 + e2), s2 * (e1 - e2),
+                                              s2 * (-e1 + e2), s2 * (-e1 - e2)], SCALES)
+    rest = np.nonzero(~ok)[0][:FINE_MAX]
+    if len(rest):
+        ang = 2 * np.pi * np.arange(FINE_DIRS) / FINE_DIRS
+        sub = {k: v[rest] for k, v in g.items()}
+        ok2, shift2 = _shift_search(case, rays8[rest], [cands[i] for i in rest], sub, depth, pieces, delta[rest],
+                                    T[rest], lambda e1, e2: [np.cos(a) * e1 + np.sin(a) * e2 for a in ang],
+                                    FINE_SCALES)
+        ok[rest] = ok2
+        shift[rest] = shift2
     return ok, shift
 
 
@@ -243,41 +276,22 @@ def compare_closest(case, depth, gpu_tu, gpu_seg, ref, pieces, gpu_leaf=None):
                    ref.get("leaf"), pieces, len(o["seg"]), int((o["seg"] >= 0).sum()))
 
 
-def band_counts(case, idx, got, depth, mode, pieces):
-    """Per-ray pruning-test counts that differ from the oracle's: whether the
-    oracle's count for one sideways-shifted copy of the ray (the shifts of
-    band_check, delta = 1e-4 r + K_FRAME 2^-24 T with r and T the largest
-    radius and control-point distance over the ray's candidates) equals the
-    GPU's.  A count sums integer outcomes of floating-point tests over the
-    whole row, so a test FP32 settles on the other side of a grazing volume
-    shows as a different count.  Returns a bool array over idx."""
-    m = len(idx)
-    if m == 0:
-        return np.zeros(0, bool)
+def count_band_delta(case):
+    """Per ray, the FP32 band of its count search: 1e-4 of the largest
+    radius plus K_FRAME 2^-24 of the largest control-point distance over the
+    ray's candidates.  oracle.ray_counts_amb flags the rays with a decision
+    (a bounding-volume test, a child order, a hit against the closest so far)
+    within that distance of flipping; a count may differ in FP32 only there."""
     rp = case["row_ptr"].astype(np.int64)
-    cands = [case["seg_idx"][rp[i]:rp[i + 1]] for i in idx]
-    rays = case["rays"][idx].astype(np.float64)
-    o_, w = rays[:, :3], rays[:, 4:7]
-    w = w / np.linalg.norm(w, axis=1, keepdims=True)
-    delta = np.zeros(m)
-    for k, c in enumerate(cands):
+    d = np.zeros(len(rp) - 1)
+    for i in range(len(d)):
+        c = case["seg_idx"][rp[i]:rp[i + 1]]
+        o_ = case["rays"][i, :3].astype(np.float64)
+        if len(c) == 0:
+            continue
         cp = case["cps"][c].astype(np.float64)
-        T = np.linalg.norm(cp[:, :, :3] - o_[k], axis=2).max() if len(c) else np.linalg.norm(o_[k])
-        r = cp[:, :, 3].max() if len(c) else 0.0
-        delta[k] = 1e-4 * r + K_FRAME * EPS32 * T
-    e1, e2 = _perp(w)
-    s2 = np.sqrt(0.5)
-    dirs = [e1, -e1, e2, -e2, s2 * (e1 + e2), s2 * (e1 - e2), s2 * (-e1 + e2), s2 * (-e1 - e2)]
-    sub_rays, rows, segs = [], [0], []
-    for sc in SCALES:
-        for dv in dirs:
-            sub_rays.append(np.concatenate([o_ + (delta * sc)[:, None] * dv, w, rays[:, 3:4]], axis=1))
-            for c in cands:
-                segs.append(c)
-                rows.append(rows[-1] + len(c))
-    ref, _ = O.ray_counts_d(np.concatenate(sub_rays), np.array(rows, dtype=np.int32),
-                            np.concatenate(segs).astype(np.int32), depth, mode, pieces)
-    return np.any(ref.reshape(-1, m) == np.asarray(got)[idx][None, :], axis=0)
+        d[i] = 1e-4 * cp[:, :, 3].max() + K_FRAME * EPS32 * np.linalg.norm(cp[:, :, :3] - o_, axis=2).max()
+    return d
 
 
 def pair_rays(case):

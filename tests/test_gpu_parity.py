@@ -116,7 +116,8 @@ def test_tiny_pairs(tiny, kernel, variant, flags):
     tu, leaf, st = _run_pairs(case, 8, kernel, variant, flags)
     assert st & ~F.FX_DEV_UNSUPPORTED == 0
     stats = P.compare_pairs(case, 8, tu, leaf, pr, pieces)
-    _assert_parity(stats, where="tiny_pairs", kernel=int(kernel), variant=int(variant), flags=int(flags))
+    _assert_parity(stats, max_band_frac=1e-4, where="tiny_pairs", kernel=int(kernel), variant=int(variant),
+                   flags=int(flags))
     assert stats["hits"] > 10000
 
 
@@ -172,14 +173,20 @@ def test_depth_sweep(klass, forced, flags, variant):
     case = I.sweep_case(klass, 4096, forced_hits=forced)
     pieces = O.presplit(case["cps"])
     fib = F.Fibers(case["cps"])
+    exempt = 0
     for depth in DEPTHS:
         ref = O.closest(case, depth, pieces)
         tu, seg, leaf, _ = _run_closest(case, depth, flags, fib, variant=variant)
         stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
-        _assert_parity(stats, where="depth_sweep", klass=klass, forced=forced, depth=depth,
+        # per depth at most 8 of the 4096 rays pass by band or silhouette
+        _assert_parity(stats, max_band_frac=2e-3, where="depth_sweep", klass=klass, forced=forced, depth=depth,
                        math="fast" if flags else "ieee", variant=int(variant))
+        exempt += stats["band"] + stats["silhouette"]
         if forced:
             assert stats["hits"] > 3500
+    # over all 21 depths at most 0.2 % (measured: at most 0.14 % for one class
+    # and math mode, 0.018 % over all of them)
+    assert exempt <= 2e-3 * len(DEPTHS) * 4096, exempt
     assert fib.status() == 0
     fib.close()
 
@@ -609,7 +616,8 @@ def test_hair_patch_full_frame(hair, flags, depth, variant):
     fib.close()
     tu, seg, leaf = _np(tu), _np(seg), _np(leaf)
     stats = P.compare_closest(case, depth, tu, seg, ref, pieces, leaf)
-    _assert_parity(stats, max_band_frac=1e-3, where="hair_full_frame", depth=depth, variant=int(variant),
+    # measured: at most 68 of the 2,073,600 rays pass by band, none by silhouette
+    _assert_parity(stats, max_band_frac=1e-4, where="hair_full_frame", depth=depth, variant=int(variant),
                    math="fast" if flags else "ieee", rays_with_candidates=int(np.count_nonzero(np.diff(case["row_ptr"]))))
     assert stats["hits"] > 100_000
     # rays with no candidates are misses
@@ -634,7 +642,8 @@ def test_hair_pairs(hair_pairs, kernel, variant, flags):
     tu, leaf, st = _run_pairs(sub, 15, kernel, variant, flags)
     assert st & ~F.FX_DEV_UNSUPPORTED == 0
     stats = P.compare_pairs(sub, 15, tu, leaf, pr, pieces)
-    _assert_parity(stats, where="hair_pairs", kernel=int(kernel), variant=int(variant), flags=int(flags))
+    _assert_parity(stats, max_band_frac=1e-4, where="hair_pairs", kernel=int(kernel), variant=int(variant),
+                   flags=int(flags))
     assert stats["hits"] > 5000
 
 
@@ -714,7 +723,7 @@ def test_host_entry_on_the_hair_frame(hair):
     assert fib.status() == 0
     fib.close()
     stats = P.compare_closest(case, 15, tu_h.numpy(), seg_h.numpy(), ref[15], pieces, leaf_h.numpy())
-    _assert_parity(stats, where="hair_host_entry")
+    _assert_parity(stats, max_band_frac=1e-4, where="hair_host_entry")
 
 
 def test_upload_from_device_memory_equals_host_upload(tiny):

@@ -114,3 +114,54 @@ def test_counts_with_double_rays_equal_float_rays(mode):
     np.testing.assert_array_equal(c_d, c_f)
     np.testing.assert_array_equal(t_d, t_f)
     assert c_f.sum() > 512
+
+
+def _band_delta(case):
+    """Per ray: 1e-4 of the largest radius plus 22 * 2^-24 of the largest
+    control-point distance over the ray's candidates (the FP32 band)."""
+    rp = case["row_ptr"].astype(np.int64)
+    d = np.zeros(len(rp) - 1)
+    for i in range(len(d)):
+        c = case["seg_idx"][rp[i]:rp[i + 1]]
+        cp = case["cps"][c].astype(np.float64)
+        T = np.linalg.norm(cp[:, :, :3] - case["rays"][i, :3].astype(np.float64), axis=2).max()
+        d[i] = 1e-4 * cp[:, :, 3].max() + 22 * 2.0 ** -24 * T
+    return d
+
+
+@pytest.mark.parametrize("klass", ["straight", "curved"])
+@pytest.mark.parametrize("mode", ["cylinder", "box"])
+def test_band_flag_covers_every_count_a_small_shift_changes(klass, mode):
+    # the flag of orc_ray_counts_amb marks rays with a decision within delta
+    # of flipping; its definition fixes that any ray whose count changes when
+    # the ray moves sideways by less than delta is flagged.  Checked with
+    # random shifts of up to delta / 4; delta = 0 flags nothing and the
+    # counts are those of the plain search
+    case = I.single_fiber_case(klass, 2048)
+    pieces = O.presplit(case["cps"])
+    dl = _band_delta(case)
+    g = np.random.default_rng(11)
+    r7 = np.stack([O.ray7_from_packed(r) for r in case["rays"]])
+    w = r7[:, 3:6] / np.linalg.norm(r7[:, 3:6], axis=1, keepdims=True)
+    a = np.where(np.abs(w[:, :1]) < 0.9, [[1.0, 0, 0]], [[0.0, 1, 0]])
+    e1 = a - np.sum(a * w, axis=1, keepdims=True) * w
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(w, e1)
+    changed_total = 0
+    for depth in (8, 16):
+        c0, _ = O.ray_counts(case, depth, mode, pieces)
+        ca, amb = O.ray_counts_amb(case, depth, mode, dl, pieces)
+        np.testing.assert_array_equal(ca, c0)
+        cz, amb0 = O.ray_counts_amb(case, depth, mode, np.zeros(len(dl)), pieces)
+        assert not amb0.any()
+        for _ in range(4):
+            ang = g.uniform(0, 2 * np.pi, len(dl))
+            m = g.uniform(0, 0.25, len(dl)) * dl
+            rs = r7.copy()
+            rs[:, :3] += (np.cos(ang)[:, None] * e1 + np.sin(ang)[:, None] * e2) * m[:, None]
+            cs, _ = O.ray_counts_d(rs, case["row_ptr"], case["seg_idx"], depth, mode, pieces)
+            ch = cs != c0
+            assert not (ch & ~amb).any(), (depth, np.nonzero(ch & ~amb)[0][:5])
+            changed_total += int(ch.sum())
+        assert amb.mean() < 0.06, amb.mean()  # the flag stays selective
+    assert changed_total > 0  # the check is not vacuous
