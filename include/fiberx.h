@@ -297,9 +297,10 @@ fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray,
  * tu / seg / leaf back and synchronises (ray_depth, when given, is a host
  * array too).  Large calls are cut into up to 4
  * chunks of rows with about equal input bytes; each chunk's copy in, kernels
- * and copy out run on two copy streams owned by the handle and on `stream`,
- * so copies overlap the other chunks' kernels (the naive kernel takes one
- * chunk).  Rays are copied only in blocks of 8192 rows that hold a
+ * and copy out run on copy and compute streams owned by the handle (after
+ * the work already queued on `stream`), so copies overlap the other chunks'
+ * kernels and a chunk's kernels overlap the tail of the chunk before (the
+ * naive kernel takes one chunk).  Rays are copied only in blocks of 8192 rows that hold a
  * candidate (the ray of an empty row is never read; its result is a miss).
  * Both rely on the CSR contract above (row_ptr[0] = 0, non-decreasing,
  * row_ptr[n_ray] = n_pair).  Host buffers should be pinned

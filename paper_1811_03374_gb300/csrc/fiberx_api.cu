@@ -376,6 +376,8 @@ void fiber_free(fx_fibers* f) {
     if (e) cudaEventDestroy(e);
   if (f->copy_in) cudaStreamDestroy(f->copy_in);
   if (f->copy_out) cudaStreamDestroy(f->copy_out);
+  for (cudaStream_t c : f->compute)
+    if (c) cudaStreamDestroy(c);
   if (f->pool) cudaMemPoolDestroy(f->pool);  // released once its last allocation is freed
   delete f;
 }
@@ -516,6 +518,7 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   if (!f->copy_in) {
     FX_CUDA(cudaStreamCreateWithFlags(&f->copy_in, cudaStreamNonBlocking));
     FX_CUDA(cudaStreamCreateWithFlags(&f->copy_out, cudaStreamNonBlocking));
+    for (cudaStream_t& c : f->compute) FX_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     for (cudaEvent_t& e : f->host_ev) FX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   char* base = (char*)f->stage;
@@ -530,9 +533,11 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
 
   // Rows are cut into up to kFxHostChunks chunks of about equal input bytes
   // (32 per ray, 4 per row_ptr entry, 4 per pair), found by bisection on the
-  // host row_ptr.  Chunk c is copied in on copy_in, intersected on the
-  // caller's stream once its copy is done, and its results copied out on
-  // copy_out, so copies overlap the other chunks' kernels.  Each chunk's
+  // host row_ptr.  Chunk c is copied in on copy_in, intersected on compute
+  // stream c mod kFxHostStreams once its copy is done, and its results copied
+  // out on copy_out, so copies overlap the other chunks' kernels, and a
+  // chunk's kernels overlap the tail of the chunk before (a kernel lasts at
+  // least as long as its longest rows' chains of scans and node steps).  Each chunk's
   // kernels read the CSR in place (row_ptr values index the whole seg_idx
   // staging), and the copies run in row order, so a chunk's pairs have
   // arrived with it.  No kernel reads the ray of an empty row, so rays are
@@ -576,6 +581,7 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   cudaEvent_t* ev_done = f->host_ev + 1 + kFxHostChunks;
   cudaError_t e = cudaEventRecord(f->host_ev[0], s);  // work queued on the caller's stream comes first
   if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_in, f->host_ev[0], 0);
+  for (int k = 0; k < kFxHostStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(f->compute[k], f->host_ev[0], 0);
   int64_t p_done = 0;
   f->host_h2d = f->host_d2h = 0;
   auto empty_block = [&](int64_t b, int64_t b_end) { return pairs_at(b) == pairs_at(b_end); };
@@ -606,13 +612,14 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
       e = cudaMemcpyAsync(d_si + p_done, seg_idx + p_done, (size_t)(p1 - p_done) * 4, cudaMemcpyHostToDevice,
                           f->copy_in);
     p_done = p1;
+    cudaStream_t cs = f->compute[c % kFxHostStreams];
     if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], f->copy_in);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[c], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in[c], 0);
     if (e != cudaSuccess || n == 0) continue;
     st = intersect_closest(f, d_rays + 8 * r0, n, d_rp + r0, d_si, n_pair, depth, d_dep ? d_dep + r0 : nullptr,
-                           flags, d_tu + 2 * r0, d_seg + r0, d_leaf ? d_leaf + r0 : nullptr, stream);
+                           flags, d_tu + 2 * r0, d_seg + r0, d_leaf ? d_leaf + r0 : nullptr, cs);
     if (st != FX_OK) break;
-    e = cudaEventRecord(ev_done[c], s);
+    e = cudaEventRecord(ev_done[c], cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_out, ev_done[c], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(tu + 2 * r0, d_tu + 2 * r0, (size_t)n * 8, cudaMemcpyDeviceToHost, f->copy_out);
@@ -624,7 +631,11 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   }
   // nothing of this call may still touch the caller's buffers on return
   const cudaError_t e_in = cudaStreamSynchronize(f->copy_in);
-  const cudaError_t e_s = cudaStreamSynchronize(s);
+  cudaError_t e_s = cudaStreamSynchronize(s);
+  for (int k = 0; k < kFxHostStreams; ++k) {
+    const cudaError_t e_k = cudaStreamSynchronize(f->compute[k]);
+    if (e_s == cudaSuccess) e_s = e_k;
+  }
   const cudaError_t e_out = cudaStreamSynchronize(f->copy_out);
   if (st != FX_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "host-buffer pipeline");

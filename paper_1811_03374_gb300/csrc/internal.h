@@ -20,6 +20,13 @@ enum {
 #define FX_HOST_CHUNKS 4
 #endif
 constexpr int kFxHostChunks = FX_HOST_CHUNKS;
+// streams the host-buffer entry runs its chunks' kernels on (round robin), so
+// that a chunk's kernels start once its own copy has landed, alongside the
+// tail of the chunk before
+#ifndef FX_HOST_STREAMS
+#define FX_HOST_STREAMS 3
+#endif
+constexpr int kFxHostStreams = FX_HOST_STREAMS;
 
 struct fx_fibers {
   int device = 0;
@@ -44,6 +51,7 @@ struct fx_fibers {
   void *stage = nullptr;
   size_t stage_bytes = 0;
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaStream_t compute[kFxHostStreams] = {};
   cudaEvent_t host_ev[1 + 2 * kFxHostChunks] = {};
   int64_t host_h2d = 0, host_d2h = 0;  // bytes the last host-buffer call copied
 };
