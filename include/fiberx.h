@@ -300,8 +300,12 @@ fx_status intersect_counts(const fx_fibers *f, const float *rays, int64_t n_ray,
  * and copy out run on copy and compute streams owned by the handle (after
  * the work already queued on `stream`), so copies overlap the other chunks'
  * kernels and a chunk's kernels overlap the tail of the chunk before (the
- * naive kernel takes one chunk).  Rays are copied only in blocks of 8192 rows that hold a
- * candidate (the ray of an empty row is never read; its result is a miss).
+ * naive kernel takes one chunk).  Rays in pinned host memory that the
+ * runtime maps into the device's address space (cudaHostAlloc, or
+ * cudaHostRegister with the mapped flag) are read by the kernels in place,
+ * 32 bytes per ray that has a candidate; other rays are copied, in blocks of
+ * 8192 rows that hold a candidate (the ray of an empty row is never read;
+ * its result is a miss).  The chunk with the fewest rays is copied last.
  * Both rely on the CSR contract above (row_ptr[0] = 0, non-decreasing,
  * row_ptr[n_ray] = n_pair).  Host buffers should be pinned
  * for full copy bandwidth and asynchronous copies.  Calls on one handle must
@@ -315,8 +319,9 @@ fx_status intersect_closest_host(fx_fibers *f, const float *rays, int64_t n_ray,
 
 /*
  * fx_host_bytes -- bytes the last intersect_closest_host call on this handle
- * copied host to device (*h2d) and device to host (*d2h); 0 before the first
- * call.  Errors: FX_EINVAL (null pointers).
+ * moved host to device (*h2d: copies, with rays read in place counted as the
+ * rays of the blocks of 8192 rows that hold a candidate) and device to host
+ * (*d2h); 0 before the first call.  Errors: FX_EINVAL (null pointers).
  */
 fx_status fx_host_bytes(const fx_fibers *f, int64_t *h2d, int64_t *d2h);
 

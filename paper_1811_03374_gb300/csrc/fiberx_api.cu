@@ -582,12 +582,51 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
   cudaError_t e = cudaEventRecord(f->host_ev[0], s);  // work queued on the caller's stream comes first
   if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_in, f->host_ev[0], 0);
   for (int k = 0; k < kFxHostStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(f->compute[k], f->host_ev[0], 0);
-  int64_t p_done = 0;
   f->host_h2d = f->host_d2h = 0;
   auto empty_block = [&](int64_t b, int64_t b_end) { return pairs_at(b) == pairs_at(b_end); };
-  for (int c = 0; c < n_chunk && e == cudaSuccess && st == FX_OK; ++c) {
+  // Rays in pinned host memory that the runtime maps into the device's
+  // address space are read by the kernels in place, over the host link, 32
+  // bytes per ray that has a candidate; other rays are copied.  The bytes are
+  // counted the same way either way (the rays of blocks of rows that hold a
+  // candidate).
+  auto mapped = [](const void* p) -> void* {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      cudaGetLastError();  // a failed query leaves no sticky error behind: copy instead
+      return nullptr;
+    }
+    return pa.type == cudaMemoryTypeHost ? pa.devicePointer : nullptr;
+  };
+  // (Results are still written to device staging and copied out: written in
+  // place over the host link they lengthen every lane's chain, measured
+  // 0.98 ms per hair frame against 0.88.)
+  const float* rays_in_place = static_cast<const float*>(mapped(rays));
+  // each chunk's range of pairs, in row order (together they cover all pairs)
+  int64_t plo[kFxHostChunks], phi[kFxHostChunks];
+  {
+    int64_t p_done = 0;
+    for (int c = 0; c < n_chunk; ++c) {
+      plo[c] = p_done;
+      phi[c] = c + 1 == n_chunk ? n_pair : std::max(p_done, pairs_at(cut[c + 1]));
+      p_done = phi[c];
+    }
+  }
+  // Copy order: row order, except that the chunk with the fewest rays goes
+  // last.  What no copy in overlaps is the last chunk's kernels and its copy
+  // out; the copy out is 12 to 16 bytes per ray, and the chunk with the
+  // fewest rays has the smallest (the candidate-free rows of an image lie in
+  // wide chunks of few pairs).
+  int order[kFxHostChunks];
+  int last = 0;
+  for (int c = 0; c < n_chunk; ++c)
+    if (cut[c + 1] - cut[c] < cut[last + 1] - cut[last]) last = c;
+  for (int c = 0, k = 0; c < n_chunk; ++c)
+    if (c != last) order[k++] = c;
+  order[n_chunk - 1] = last;
+  for (int k = 0; k < n_chunk && e == cudaSuccess && st == FX_OK; ++k) {
+    const int c = order[k];
     const int64_t r0 = cut[c], r1 = cut[c + 1], n = r1 - r0;
-    const int64_t p1 = c + 1 == n_chunk ? n_pair : std::max(p_done, pairs_at(r1));
+    const int64_t p_done = plo[c], p1 = phi[c];
     for (int64_t b = r0; b < r1 && e == cudaSuccess;) {
       int64_t run_end = std::min(b + kRayBlock, r1);
       if (empty_block(b, run_end)) {
@@ -596,12 +635,13 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
       }
       while (run_end < r1 && !empty_block(run_end, std::min(run_end + kRayBlock, r1)))
         run_end = std::min(run_end + kRayBlock, r1);
-      e = cudaMemcpyAsync(d_rays + 8 * b, rays + 8 * b, (size_t)(run_end - b) * 32, cudaMemcpyHostToDevice,
-                          f->copy_in);
+      if (!rays_in_place)
+        e = cudaMemcpyAsync(d_rays + 8 * b, rays + 8 * b, (size_t)(run_end - b) * 32, cudaMemcpyHostToDevice,
+                            f->copy_in);
       f->host_h2d += (run_end - b) * 32;
       b = run_end;
     }
-    f->host_h2d += (n + 1) * 4 + (p1 - p_done) * 4;
+    f->host_h2d += (n + 1) * 4 + std::max<int64_t>(0, p1 - p_done) * 4;
     if (e == cudaSuccess && d_dep && n > 0) {
       e = cudaMemcpyAsync(d_dep + r0, ray_depth + r0, (size_t)n, cudaMemcpyHostToDevice, f->copy_in);
       f->host_h2d += n;
@@ -611,14 +651,15 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
     if (e == cudaSuccess && p1 > p_done)
       e = cudaMemcpyAsync(d_si + p_done, seg_idx + p_done, (size_t)(p1 - p_done) * 4, cudaMemcpyHostToDevice,
                           f->copy_in);
-    p_done = p1;
-    cudaStream_t cs = f->compute[c % kFxHostStreams];
+    cudaStream_t cs = f->compute[k % kFxHostStreams];
     if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], f->copy_in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in[c], 0);
     if (e != cudaSuccess || n == 0) continue;
-    st = intersect_closest(f, d_rays + 8 * r0, n, d_rp + r0, d_si, n_pair, depth, d_dep ? d_dep + r0 : nullptr,
-                           flags, d_tu + 2 * r0, d_seg + r0, d_leaf ? d_leaf + r0 : nullptr, cs);
+    st = intersect_closest(f, (rays_in_place ? rays_in_place : d_rays) + 8 * r0, n, d_rp + r0, d_si, n_pair, depth,
+                           d_dep ? d_dep + r0 : nullptr, flags, d_tu + 2 * r0, d_seg + r0,
+                           d_leaf ? d_leaf + r0 : nullptr, cs);
     if (st != FX_OK) break;
+    f->host_d2h += n * (leaf ? 16 : 12);
     e = cudaEventRecord(ev_done[c], cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_out, ev_done[c], 0);
     if (e == cudaSuccess)
@@ -627,7 +668,6 @@ fx_status intersect_closest_host(fx_fibers* f, const float* rays, int64_t n_ray,
       e = cudaMemcpyAsync(seg + r0, d_seg + r0, (size_t)n * 4, cudaMemcpyDeviceToHost, f->copy_out);
     if (e == cudaSuccess && leaf)
       e = cudaMemcpyAsync(leaf + r0, d_leaf + r0, (size_t)n * 4, cudaMemcpyDeviceToHost, f->copy_out);
-    f->host_d2h += n * (leaf ? 16 : 12);
   }
   // nothing of this call may still touch the caller's buffers on return
   const cudaError_t e_in = cudaStreamSynchronize(f->copy_in);

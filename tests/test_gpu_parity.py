@@ -430,15 +430,25 @@ def _chunked_case():
                          ids=["lane", "scan-fast", "lane-polish", "naive"])
 def test_host_entry_pipeline_matches_device(variant, flags):
     # the chunked copy / compute pipeline of the host entry gives the device
-    # entry's results bit for bit
+    # entry's results bit for bit, with the rays copied (pageable memory) or
+    # read in place by the kernels (pinned memory)
     case = _chunked_case()
     fib = F.Fibers(case["cps"])
     fib.set_launch(variant=variant)
     tu_d, seg_d, leaf_d = F.intersect_closest(fib, case["rays"], case["row_ptr"], case["seg_idx"], 12, flags)
     torch.cuda.synchronize()
     h = tuple(torch.from_numpy(np.asarray(x)).pin_memory() for x in (case["rays"], case["row_ptr"], case["seg_idx"]))
-    for _ in range(2):  # the second call reuses the staging and the streams
-        tu_h, seg_h, leaf_h = F.intersect_closest_host(fib, *h, 12, flags)
+    n = len(case["rays"])
+    pinned_out = (torch.empty((n, 2)).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory(),
+                  torch.empty(n, dtype=torch.int32).pin_memory())
+    # pinned inputs (the kernels read the rays in place); pageable outputs,
+    # then pinned ones; the second call of each reuses the staging and the
+    # streams
+    for out in (None, None, pinned_out, pinned_out):
+        if out is not None:
+            for t in out:
+                t.fill_(-7)  # every element must be written by the call
+        tu_h, seg_h, leaf_h = F.intersect_closest_host(fib, *h, 12, flags, out=out)
         np.testing.assert_array_equal(_np(tu_d), tu_h.numpy())
         np.testing.assert_array_equal(_np(seg_d), seg_h.numpy())
         np.testing.assert_array_equal(_np(leaf_d), leaf_h.numpy())
