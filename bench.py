@@ -153,6 +153,8 @@ class NvmlClocks:
         self._stop.set()
         self._thread.join()
         self._sample()  # at least one sample at the end of the region
+        self._nv.nvmlShutdown()
+        self.ok = False
         if not self.samples:
             return None
         sm = np.array([x[1] for x in self.samples])

@@ -46,3 +46,15 @@ def test_work_per_launch_is_the_sum_of_event_costs():
     # the paper's algorithm sets up and root-tests every candidate: never less work
     assert FL.method_flops(c, 50) > FL.alg_flops(c, 50)
     assert FL.fp32_peak_tflops(152, 2070.0) == 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def test_clock_sampler_reports_or_stays_silent():
+    # NVML where it loads (read-only queries from a thread), nvidia-smi
+    # otherwise; without either (a machine with no GPU) the record is None,
+    # never an error.  A record names its source and its reasons.
+    c = bench.clock_sampler(0)
+    rec = c.stop(0.5)
+    if rec is not None:
+        assert rec["source"] in ("nvml", "nvidia-smi")
+        assert rec["samples"] >= 1 and rec["sm_mhz"] > 0 and isinstance(rec["reasons"], list)
+        assert abs(rec["kcycles_per_step_at_median"] - 0.5 * rec["sm_mhz"]) < 1e-9
