@@ -402,6 +402,7 @@ def main():
     n_piece_touched = int(len(np.unique(case["seg_idx"])))
     work = FL.alg_flops(counters, n_ray_cand)
     mwork = FL.method_flops(counters, n_ray_cand)
+    ework = FL.estimate_flops(counters, n_ray_cand)
     abytes = FL.alg_bytes(n_ray, n_pair, n_piece_touched)
 
     graph = None
@@ -499,6 +500,9 @@ def main():
                 # test; every candidate set up and its root tested), at this time
                 "method_flops_per_launch": mwork,
                 "frac_method_equivalent": mwork / (ms_step * 1e-3) / 1e12 / peak,
+                # the same with per-unit estimates from App. C's operation counts
+                "estimate_flops_per_launch": ework,
+                "frac_per_unit_estimate": ework / (ms_step * 1e-3) / 1e12 / peak,
                 "hbm_gbs_algorithmic": abytes / (ms_step * 1e-3) / 1e9,
                 "alg_bytes_per_launch": abytes}
     if winst:

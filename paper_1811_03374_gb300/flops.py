@@ -28,6 +28,18 @@ test like any node (method_flops):
 Descents, backtracks and hits are the same events on both: the bound test
 only removes root tests that cannot pass.
 
+A third, coarser count takes per-unit estimates from the operation counts
+of App. C's routines instead of the kernels' arithmetic (estimate_flops),
+for the paper's algorithm on the same events:
+
+  per ray with candidates   ONB: about 12 operations + 1 reciprocal      13
+  per candidate             setup of Sec. 3.1 / 3.3                      75
+  per node test             test and partition/descent: about 120 flops
+                            + 3 reciprocals + 2 square roots (every
+                            candidate's root tested as a node)          125
+  per backtrack             recomputation: 105 operations + 2 rcp        107
+  per hit                   final: 12 operations + 1 division            13
+
 Counters (all variants): tests = candidate pieces examined, nodes = node
 tests including roots, descents, backtracks, hits.  Every deeper node test
 follows a descent or a backtrack, so root node tests = nodes - descents -
@@ -43,6 +55,12 @@ PER_BACKTRACK = 157
 PER_HIT = 17
 
 PER_SETUP_METHOD = 99
+
+EST_RAY = 13
+EST_SETUP = 75
+EST_NODE = 125
+EST_BACKTRACK = 107
+EST_HIT = 13
 
 # Bytes a closest-hit launch must move at least once: ray (32 B) and two
 # row_ptr words per ray, one seg_idx word per pair, 64 B per piece touched,
@@ -67,6 +85,15 @@ def method_flops(counters, n_ray_with_candidates):
     deeper = c["descents"] + c["backtracks"]
     return (PER_RAY * n_ray_with_candidates + (PER_SETUP_METHOD + PER_NODE) * c["tests"] + PER_NODE * deeper
             + PER_DESCENT * c["descents"] + PER_BACKTRACK * c["backtracks"] + PER_HIT * c["hits"])
+
+
+def estimate_flops(counters, n_ray_with_candidates):
+    """The paper's algorithm on the same events, with the per-unit estimates
+    from the operation counts of App. C (see the module docstring)."""
+    c = counters
+    deeper = c["descents"] + c["backtracks"]
+    return (EST_RAY * n_ray_with_candidates + EST_SETUP * c["tests"] + EST_NODE * (c["tests"] + deeper)
+            + EST_BACKTRACK * c["backtracks"] + EST_HIT * c["hits"])
 
 
 def alg_bytes(n_ray, n_pair, n_piece_touched):

@@ -46,6 +46,9 @@ def test_work_per_launch_is_the_sum_of_event_costs():
     # the paper's algorithm sets up and root-tests every candidate: never less work
     assert FL.method_flops(c, 50) > FL.alg_flops(c, 50)
     assert FL.fp32_peak_tflops(152, 2070.0) == 152 * 128 * 2 * 2070e6 / 1e12
+    # per-unit estimates: every candidate set up and root-tested as a node
+    assert FL.estimate_flops(c, 50) == (FL.EST_RAY * 50 + FL.EST_SETUP * 1000 + FL.EST_NODE * (1000 + 35)
+                                        + FL.EST_BACKTRACK * 5 + FL.EST_HIT * 7)
 
 
 def test_clock_sampler_reports_or_stays_silent():
