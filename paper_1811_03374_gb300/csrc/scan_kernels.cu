@@ -63,7 +63,7 @@ static_assert(kS >= 1 && kS <= 8, "1 to 8 windows per iteration");
 // root hits of a window handed to its owner at once; a window with more
 // resumes at the next one
 #ifndef FX_SCAN_PL
-#define FX_SCAN_PL 4
+#define FX_SCAN_PL 5
 #endif
 constexpr int kPL = FX_SCAN_PL;
 // relative slack of the bound test against FP32 rounding of the rotation
@@ -133,19 +133,27 @@ __global__ void __launch_bounds__(256) k_rows(const TraceArgs a, const ScanArgs 
   }
 }
 
-template <bool FAST, bool PAIRS, bool COUNT>
-__global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceArgs a, const ScanArgs o, int check) {
+// Shared memory stays under 32 KB per CTA (31.5 KB for closest hits), so
+// that five CTAs fit the 164 KB shared-memory configuration of an SM and
+// leave the rest of its 256 KB to the L1 cache that serves the piece loads
+// (a 34.8 KB layout, which needs the 196 KB configuration, measured 3 %
+// slower on the hair frame).
+template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
+__global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceArgs a, const ScanArgs o) {
+  constexpr int check = CHECK ? 1 : 0;
   // per lane's ray: {o.xyz, closest hit so far t}, {w.xyz, ray t_max (pairs) or
   // hit leaf}, {e1.xyz, hit u}, {e2.xyz, hit segment}; the hit's u, leaf and
   // segment stay here rather than in registers until the ray is finished
   __shared__ __align__(16) float4 s_fr[4][kScanBlock];
-  // root records of the windows at the test stage: [window][p | d][lane],
-  // and their segment ids
+  // root records of the windows at the test stage: [window][p | d][lane]
+  // (their segment ids stay in registers)
   __shared__ __align__(16) float4 s_rec[kS][2][kScanBlock];
-  __shared__ int32_t s_ids[kS][kScanBlock];
-  // per lane: its window's root hits, in row order, as {segment, left-hand
-  // side of the bound test, root radius, candidate index}
-  __shared__ __align__(16) int4 s_pl[kPL][kScanBlock];
+  // per lane: its window's root hits, in row order: segment, left-hand side
+  // of the bound test, root radius and (per-pair results) candidate index
+  __shared__ int32_t s_pls[kPL][kScanBlock];
+  __shared__ float s_pll[kPL][kScanBlock];
+  __shared__ float s_plr[kPL][kScanBlock];
+  __shared__ int32_t s_plj[PAIRS ? kPL : 1][kScanBlock];
   const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
   const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -155,12 +163,12 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
 
   int32_t ray = -1, cend = 0;
   int32_t wpos = 0;    // first candidate of the row not scanned yet
-  int32_t pl_next = 0, pl_end = 0;  // root hits of the window not traversed yet: s_pl[pl_next, pl_end)
+  int32_t pl_next = 0, pl_end = 0;  // root hits of the window not traversed yet: entries [pl_next, pl_end)
   bool scanning = false;  // this lane's next window is in the scan pipeline
   // scan pipeline (warp-uniform lane sets; a window's slot is its owner's
   // rank in the set): hA -- ids loaded into idA, hB -- records in flight
   unsigned hA = 0u, hB = 0u;
-  int32_t idA[kS];
+  int32_t idA[kS], idB[kS];  // ids of the windows in hA, in hB
   float ray_tmax = 0.0f, best_t = 0.0f;
   bool active = false;
 
@@ -200,10 +208,11 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
   auto begin_next = [&]() -> bool {
     const float lim = PAIRS ? ray_tmax : best_t;
     while (pl_next < pl_end) {
-      const int4 e = s_pl[pl_next][tid];
+      const int32_t s = s_pls[pl_next][tid];
+      const float lhs = s_pll[pl_next][tid], rr = s_plr[pl_next][tid];
+      const int32_t j = PAIRS ? s_plj[pl_next][tid] : 0;
       ++pl_next;
-      if (!PAIRS && __int_as_float(e.y) > lim) continue;
-      const int32_t s = e.x;
+      if (!PAIRS && lhs > lim) continue;
       const float4* pc = a.piece + 4 * (int64_t)s;
       const float4 p = __ldg(pc), d = __ldg(pc + 1), t0 = __ldg(pc + 2), t1 = __ldg(pc + 3);
       const RayFrame r = frame();
@@ -212,8 +221,8 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
       c.t0 = rotate(r, t0.x, t0.y, t0.z, t0.w);
       c.t1 = rotate(r, t1.x, t1.y, t1.z, t1.w);
       s_cur = s;
-      cand_j = e.w;
-      root_r = __int_as_float(e.z);
+      cand_j = j;
+      root_r = rr;
       bits = 0;
       start = 0;
       size = kRootSize;
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
       const int32_t end = __shfl_sync(kFull, cend, L);
       const int slot = warp0 + L;
       const int32_t j = base + lane;
-      const int32_t s = s_ids[q][tid];
+      const int32_t s = idB[q];
       const bool valid = j < end && s >= 0 && (!check || s < a.n_seg);
       bool pass = false;
       float lhs = 0.0f, rr = 0.0f;
@@ -282,7 +291,10 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
         resume = base + __ffs(mm) - 1;
       }
       if (pass && rank < kPL) {
-        s_pl[rank][slot] = make_int4(s, __float_as_int(lhs), __float_as_int(rr), j);
+        s_pls[rank][slot] = s;
+        s_pll[rank][slot] = lhs;
+        s_plr[rank][slot] = rr;
+        if (PAIRS) s_plj[rank][slot] = j;
         prefetch_l1(a.piece + 4 * (int64_t)s);
       }
       if (j < end && j < resume) {
@@ -307,14 +319,14 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
     hB = 0u;
   };
   // Copy stage: root records of the windows in hA (ids in idA) to shared
-  // memory; they move to hB.
+  // memory; they move to hB (ids to idB).
   auto scan_copy = [&]() {
     const int n = __popc(hA);
 #pragma unroll
     for (int q = 0; q < kS; ++q) {
       if (q >= n) break;  // warp-uniform
       const int32_t s = idA[q];
-      s_ids[q][tid] = s;
+      idB[q] = s;
       if (s >= 0 && (!check || s < a.n_seg)) {
         cp16(&s_rec[q][0][tid], a.piece_root + 2 * (int64_t)s);
         cp16(&s_rec[q][1][tid], a.piece_root + 2 * (int64_t)s + 1);
@@ -482,24 +494,29 @@ __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceAr
   }
 }
 
-template <bool FAST, bool PAIRS, bool COUNT>
-cudaError_t launch_s(const TraceArgs& a, const ScanArgs& o, int check, int bps_cap, int sms, cudaStream_t s) {
-  k_rows<PAIRS><<<sms * 8, 256, 0, s>>>(a, o, check);
+template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
+cudaError_t launch_s(const TraceArgs& a, const ScanArgs& o, int bps_cap, int sms, cudaStream_t s) {
+  k_rows<PAIRS><<<sms * 8, 256, 0, s>>>(a, o, CHECK ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan<FAST, PAIRS, COUNT>, kScanBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan<FAST, PAIRS, COUNT, CHECK>, kScanBlock, 0);
   if (occ < 1) occ = 1;
   if (bps_cap > 0 && bps_cap < occ) occ = bps_cap;
-  k_scan<FAST, PAIRS, COUNT><<<sms * occ, kScanBlock, 0, s>>>(a, o, check);
+  k_scan<FAST, PAIRS, COUNT, CHECK><<<sms * occ, kScanBlock, 0, s>>>(a, o);
   return cudaGetLastError();
+}
+
+template <bool FAST, bool PAIRS, bool COUNT>
+cudaError_t launch_s1(const TraceArgs& a, const ScanArgs& o, uint32_t flags, int bps, int sms, cudaStream_t s) {
+  return (flags & FX_CHECK_INDEX) ? launch_s<FAST, PAIRS, COUNT, true>(a, o, bps, sms, s)
+                                  : launch_s<FAST, PAIRS, COUNT, false>(a, o, bps, sms, s);
 }
 
 template <bool FAST, bool PAIRS>
 cudaError_t launch_s2(const TraceArgs& a, const ScanArgs& o, uint32_t flags, int bps, int sms, cudaStream_t s) {
-  const int chk = (flags & FX_CHECK_INDEX) ? 1 : 0;
-  return (flags & FX_COUNT) ? launch_s<FAST, PAIRS, true>(a, o, chk, bps, sms, s)
-                            : launch_s<FAST, PAIRS, false>(a, o, chk, bps, sms, s);
+  return (flags & FX_COUNT) ? launch_s1<FAST, PAIRS, true>(a, o, flags, bps, sms, s)
+                            : launch_s1<FAST, PAIRS, false>(a, o, flags, bps, sms, s);
 }
 
 }  // namespace
