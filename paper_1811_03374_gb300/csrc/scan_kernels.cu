@@ -133,11 +133,11 @@ __global__ void __launch_bounds__(256) k_rows(const TraceArgs a, const ScanArgs 
   }
 }
 
-// Shared memory stays under 32 KB per CTA (31.5 KB for closest hits), so
-// that five CTAs fit the 164 KB shared-memory configuration of an SM and
-// leave the rest of its 256 KB to the L1 cache that serves the piece loads
-// (a 34.8 KB layout, which needs the 196 KB configuration, measured 3 %
-// slower on the hair frame).
+// Shared memory is 31.5 KB per CTA, so that five CTAs, with the 1 KB each
+// reserves, fit the SM's 168 KB shared-memory configuration rather than the
+// 196 KB one (the former 34.8 KB layout, with the ids in shared memory and
+// the candidate index in every list entry, measured 2 % slower on the hair
+// frame at the same list length).
 template <bool FAST, bool PAIRS, bool COUNT, bool CHECK>
 __global__ void __launch_bounds__(kScanBlock, FX_SCAN_MINB) k_scan(const TraceArgs a, const ScanArgs o) {
   constexpr int check = CHECK ? 1 : 0;
