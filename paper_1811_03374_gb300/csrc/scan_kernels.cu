@@ -12,8 +12,8 @@
 // the cylinder of the precomputed conservative radius).  A ballot ranks the
 // candidates whose root cylinder is hit; the first kPL of them go, in row
 // order, to a short list of the owner's in shared memory (segment, the bound
-// test's left-hand side, root radius, candidate index), and if there are
-// more, the owner's row resumes at the next one.  Candidates rejected in the
+// test's left-hand side, root radius, and for per-pair results the candidate
+// index), and if there are more, the owner's row resumes at the next one.  Candidates rejected in the
 // scan cost a thirty-second of a warp step each instead of a full lane step.
 //
 // A rows pass runs first: it writes the misses of the rays without
